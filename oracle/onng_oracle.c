@@ -1,0 +1,884 @@
+/*
+ * CPU FP64 oracle for the degree-adjusted kNN-graph method of Iwasaki & Miyazaki,
+ * "Optimization of Indexing Based on k-Nearest Neighbor Graph for Proximity Search
+ * in High-dimensional Data" (arXiv 1810.07355).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the CUDA
+ * library is checked against.  Only the tests, the smoke check and the CPU-baseline
+ * leg of the benchmark may load it; the library itself never does.  It shares no
+ * code, header or table with the CUDA sources.
+ *
+ * Every distance is Euclidean, computed in double precision by direct difference
+ * sqrt(sum_j (x_j - y_j)^2) from the float32 inputs.  Lists are ordered by
+ * (distance, id); ties are broken by the smaller id (the paper is silent on ties).
+ *
+ * Functions and the passages they follow:
+ *   oracle_knn            exact k-nearest neighbours (textbook definition; the
+ *                         exact graph replaces the paper's ANNG-derived AKNNG, Sec. 2.5)
+ *   oracle_adjust_degree  static degree adjustment, Algorithm 2 (set form, Sec. 2.1)
+ *   oracle_adjust_path    path adjustment, Algorithms 4/5 read order-free (Sec. 2.3)
+ *   oracle_adjust_path_alg4  Algorithm 4 taken literally (round-robin, ascending ids)
+ *   oracle_search         KnnSearch, Algorithm 1, with the visited set of
+ *                         Algorithms Set/IsSet (Sec. 2.5) and e_p of Eq. 1 as e_s
+ *   oracle_seeds_random   random seed rule (the paper's "rand" seeds, Sec. 3)
+ *   oracle_seeds_pivot    nearest-pivot seed rule (stands in for the vp-tree
+ *                         seeds of Sec. 2 / Table 5, which the paper leaves unspecified)
+ *   oracle_bf16_round     bfloat16 round-to-nearest-even of float32 inputs
+ *   oracle_mlp_*          the per-query (eps, e_s) predictor network (no paper
+ *                         counterpart; the paper's fixed policy is Eq. 1)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_OK 0
+#define ORACLE_E_INVAL 1
+#define ORACLE_E_NOMEM 2
+
+/* ---------------------------------------------------------------- distances */
+
+static double dist64(const float *a, const float *b, int d)
+{
+    double s = 0.0;
+    for (int j = 0; j < d; ++j) {
+        double t = (double)a[j] - (double)b[j];
+        s += t * t;
+    }
+    return sqrt(s);
+}
+
+/* (da, ia) < (db, ib) in lexicographic (distance, id) order */
+static int lt_pair(double da, int64_t ia, double db, int64_t ib)
+{
+    return da < db || (da == db && ia < ib);
+}
+
+/* ------------------------------------------------------------ exact kNN (O1) */
+
+/* Insert (dv, iv) into the ascending list (dl, il) of current length *cnt and
+ * capacity k; the largest element falls off when the list is full. */
+static void sorted_insert(double *dl, int32_t *il, int *cnt, int k, double dv, int32_t iv)
+{
+    int c = *cnt;
+    if (c == k && !lt_pair(dv, iv, dl[k - 1], il[k - 1]))
+        return;
+    int pos = (c < k) ? c : k - 1;
+    while (pos > 0 && lt_pair(dv, iv, dl[pos - 1], il[pos - 1])) {
+        dl[pos] = dl[pos - 1];
+        il[pos] = il[pos - 1];
+        --pos;
+    }
+    dl[pos] = dv;
+    il[pos] = iv;
+    if (c < k)
+        *cnt = c + 1;
+}
+
+/*
+ * For each query row q_r (r < nq) the k base points nearest to it, ordered by
+ * (distance, id).  If self_ids is non-NULL, base point self_ids[r] is excluded
+ * from row r (the query is that base point itself; a duplicate point at
+ * distance 0 with another id is still a neighbour).  Rows with fewer than k
+ * candidates are padded with id -1 and distance +inf.
+ */
+int oracle_knn(const float *base, int64_t n, int d, const float *Q, int64_t nq,
+               const int64_t *self_ids, int k, int32_t *nbr, double *len, int threads)
+{
+    if (n < 0 || nq < 0 || d <= 0 || k <= 0)
+        return ORACLE_E_INVAL;
+#ifdef _OPENMP
+    if (threads > 0)
+        omp_set_num_threads(threads);
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+    for (int64_t r = 0; r < nq; ++r) {
+        const float *q = Q + r * (int64_t)d;
+        double *dl = len + r * (int64_t)k;
+        int32_t *il = nbr + r * (int64_t)k;
+        int cnt = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (self_ids && self_ids[r] == j)
+                continue;
+            sorted_insert(dl, il, &cnt, k, dist64(q, base + j * (int64_t)d, d), (int32_t)j);
+        }
+        for (int t = cnt; t < k; ++t) {
+            dl[t] = INFINITY;
+            il[t] = -1;
+        }
+    }
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------- static degree adjustment (O2) */
+
+typedef struct {
+    int32_t id;
+    double len;
+} edge_t;
+
+static int cmp_edge(const void *a, const void *b)
+{
+    const edge_t *x = (const edge_t *)a, *y = (const edge_t *)b;
+    if (x->len < y->len) return -1;
+    if (x->len > y->len) return 1;
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+/*
+ * Algorithm 2 (ConstructAdjustedGraph) in its set form: the adjusted list of a
+ * node o is
+ *     N_e(o) = first_{e_o}(N_k(o))  united with  { x : o in first_{e_i}(N_k(x)) }.
+ * The loop bound of Algorithm 2 is read as p <= max(e_o, e_i): the literal
+ * "p <= e_o and p <= e_i" would make the two inner tests vacuous and would turn
+ * the call with (k_c, 0) of Algorithm ConstructGraph into an empty graph.
+ * A reversed edge x->o carries the stored length of o->x; when x->o is also a
+ * forward edge of x, the forward edge's own stored length is kept.  Every list
+ * is sorted by (length, id) because the search relies on length-ordered lists.
+ *
+ * Input: the kNN lists nbr/len of shape [n, k], each row ordered by (length, id),
+ * ids -1 allowed as padding at the end of a row.  Only the rows listed in
+ * `rows` (nrows of them; rows == NULL means all n) are produced, in CSR form:
+ * out_ptr [nrows + 1], out_col / out_len of capacity `cap`.  Returns the number
+ * of edges written, or -1 if cap is too small or an argument is invalid.
+ */
+int64_t oracle_adjust_degree(const int32_t *nbr, const double *len, int64_t n, int k,
+                             int e_o, int e_i, const int64_t *rows, int64_t nrows,
+                             int64_t *out_ptr, int32_t *out_col, double *out_len, int64_t cap)
+{
+    if (n < 0 || k <= 0 || e_o < 0 || e_i < 0)
+        return -1;
+    int fo = e_o < k ? e_o : k;
+    int fi = e_i < k ? e_i : k;
+    if (rows == NULL)
+        nrows = n;
+    /* position of every node among the requested rows (-1 = not requested) */
+    int64_t *slot = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int64_t *incnt = (int64_t *)calloc((size_t)(nrows + 1), sizeof(int64_t));
+    if (!slot || !incnt) {
+        free(slot);
+        free(incnt);
+        return -1;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        slot[i] = rows ? -1 : i;
+    if (rows)
+        for (int64_t r = 0; r < nrows; ++r)
+            slot[rows[r]] = r;
+    /* reversed edges: count, then gather, in ascending x */
+    for (int64_t x = 0; x < n; ++x)
+        for (int p = 0; p < fi; ++p) {
+            int32_t o = nbr[x * k + p];
+            if (o >= 0 && slot[o] >= 0)
+                incnt[slot[o]]++;
+        }
+    int64_t *inptr = (int64_t *)malloc((size_t)(nrows + 1) * sizeof(int64_t));
+    int64_t total_in = 0;
+    for (int64_t r = 0; r < nrows; ++r) {
+        inptr[r] = total_in;
+        total_in += incnt[r];
+    }
+    inptr[nrows] = total_in;
+    edge_t *inl = (edge_t *)malloc((size_t)(total_in > 0 ? total_in : 1) * sizeof(edge_t));
+    memset(incnt, 0, (size_t)(nrows + 1) * sizeof(int64_t));
+    for (int64_t x = 0; x < n; ++x)
+        for (int p = 0; p < fi; ++p) {
+            int32_t o = nbr[x * k + p];
+            if (o >= 0 && slot[o] >= 0) {
+                int64_t r = slot[o];
+                inl[inptr[r] + incnt[r]].id = (int32_t)x;
+                inl[inptr[r] + incnt[r]].len = len[x * k + p];
+                incnt[r]++;
+            }
+        }
+    int64_t w = 0;
+    int64_t ret = 0;
+    edge_t *buf = NULL;
+    int64_t bufcap = 0;
+    for (int64_t r = 0; r < nrows && ret == 0; ++r) {
+        int64_t o = rows ? rows[r] : r;
+        int64_t m = 0;
+        int64_t need = fo + (inptr[r + 1] - inptr[r]);
+        if (need > bufcap) {
+            free(buf);
+            bufcap = need * 2 + 16;
+            buf = (edge_t *)malloc((size_t)bufcap * sizeof(edge_t));
+        }
+        /* forward edges first: they win over a reversed duplicate */
+        for (int p = 0; p < fo; ++p) {
+            int32_t x = nbr[o * k + p];
+            if (x < 0)
+                continue;
+            buf[m].id = x;
+            buf[m].len = len[o * k + p];
+            ++m;
+        }
+        int64_t nf = m;
+        for (int64_t t = inptr[r]; t < inptr[r + 1]; ++t) {
+            int dup = 0;
+            for (int64_t u = 0; u < nf; ++u)
+                if (buf[u].id == inl[t].id) {
+                    dup = 1;
+                    break;
+                }
+            if (!dup)
+                buf[m++] = inl[t];
+        }
+        qsort(buf, (size_t)m, sizeof(edge_t), cmp_edge);
+        out_ptr[r] = w;
+        if (w + m > cap) {
+            ret = -1;
+            break;
+        }
+        for (int64_t u = 0; u < m; ++u) {
+            out_col[w + u] = buf[u].id;
+            out_len[w + u] = buf[u].len;
+        }
+        w += m;
+    }
+    if (ret == 0)
+        out_ptr[nrows] = w;
+    free(buf);
+    free(inl);
+    free(inptr);
+    free(incnt);
+    free(slot);
+    return ret == 0 ? w : -1;
+}
+
+/* ------------------------------------------------------ path adjustment (O3) */
+
+/* stored length of edge a->b in CSR (ptr, col, len), or NAN if absent */
+static double edge_len(const int64_t *ptr, const int32_t *col, const double *len, int64_t a, int32_t b)
+{
+    for (int64_t t = ptr[a]; t < ptr[a + 1]; ++t)
+        if (col[t] == b)
+            return len[t];
+    return NAN;
+}
+
+/*
+ * Path adjustment, order-free reading of Algorithms 4 and 5: an edge (i, j) of
+ * the input graph is dropped when the input graph has a two-hop path i->m->j
+ * whose two hops are both strictly shorter than (i, j):
+ *     len(i,m) < len(i,j)  and  len(m,j) < len(i,j).
+ * All tests run on the input graph (not on the partial output of Algorithm 4),
+ * so the result does not depend on any processing order.  Kept edges stay in
+ * their input order.  Produces the rows listed in `rows` (NULL = all) in CSR
+ * form; returns the number of edges kept, or -1 on a too small `cap`.
+ * If `removed_by` is non-NULL, it receives for every input edge of the listed
+ * rows (in input order, concatenated) the witness m of its removal, or -1.
+ */
+int64_t oracle_adjust_path(const int64_t *ptr, const int32_t *col, const double *len, int64_t n,
+                           const int64_t *rows, int64_t nrows, int64_t *out_ptr, int32_t *out_col,
+                           double *out_len, int64_t cap, int32_t *removed_by)
+{
+    if (rows == NULL)
+        nrows = n;
+    int64_t w = 0, e = 0;
+    for (int64_t r = 0; r < nrows; ++r) {
+        int64_t i = rows ? rows[r] : r;
+        out_ptr[r] = w;
+        for (int64_t t = ptr[i]; t < ptr[i + 1]; ++t) {
+            int32_t j = col[t];
+            double lij = len[t];
+            int32_t witness = -1;
+            for (int64_t u = ptr[i]; u < ptr[i + 1] && witness < 0; ++u) {
+                int32_t m = col[u];
+                if (m == j || !(len[u] < lij))
+                    continue;
+                double lmj = edge_len(ptr, col, len, m, j);
+                if (!isnan(lmj) && lmj < lij)
+                    witness = m;
+            }
+            if (removed_by)
+                removed_by[e] = witness;
+            ++e;
+            if (witness >= 0)
+                continue;
+            if (w >= cap)
+                return -1;
+            out_col[w] = j;
+            out_len[w] = lij;
+            ++w;
+        }
+    }
+    out_ptr[nrows] = w;
+    return w;
+}
+
+/*
+ * Algorithm 4 (AdjustPath) taken literally, as a reported variant: in rounds,
+ * every node that still has unprocessed edges takes its shortest remaining edge
+ * (n, n_d) and keeps it unless HasPath (Algorithm 5) finds, in the partial output
+ * graph G_p, a neighbour m of n with n_d in N(G_p, m) and len(m, n_d) < len(n, n_d).
+ * Nodes are visited in ascending id inside a round (the paper leaves the order
+ * open).  Output lists are in the order edges were added, which is ascending
+ * length per node.  Whole graph only; returns the edge count or -1.
+ */
+int64_t oracle_adjust_path_alg4(const int64_t *ptr, const int32_t *col, const double *len, int64_t n,
+                                int64_t *out_ptr, int32_t *out_col, double *out_len, int64_t cap)
+{
+    int64_t nnz = ptr[n];
+    if (cap < nnz)
+        return -1;
+    /* G_p is kept in per-node slices of the output arrays sized like the input */
+    int64_t *cnt = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+    int32_t *gcol = (int32_t *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
+    double *glen = (double *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(double));
+    int64_t *next = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    if (!cnt || !gcol || !glen || !next) {
+        free(cnt); free(gcol); free(glen); free(next);
+        return -1;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        next[i] = ptr[i]; /* input lists are already in (length, id) order */
+    int active = 1;
+    while (active) {
+        active = 0;
+        for (int64_t s = 0; s < n; ++s) {
+            if (next[s] >= ptr[s + 1])
+                continue;
+            active = 1;
+            int32_t nd = col[next[s]];
+            double lsd = len[next[s]];
+            int has = 0;
+            for (int64_t u = 0; u < cnt[s] && !has; ++u) {
+                int32_t m = gcol[ptr[s] + u];
+                for (int64_t v = 0; v < cnt[m]; ++v)
+                    if (gcol[ptr[m] + v] == nd && glen[ptr[m] + v] < lsd) {
+                        has = 1;
+                        break;
+                    }
+            }
+            if (!has) {
+                gcol[ptr[s] + cnt[s]] = nd;
+                glen[ptr[s] + cnt[s]] = lsd;
+                cnt[s]++;
+            }
+            next[s]++;
+        }
+    }
+    int64_t w = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        out_ptr[i] = w;
+        for (int64_t u = 0; u < cnt[i]; ++u) {
+            out_col[w] = gcol[ptr[i] + u];
+            out_len[w] = glen[ptr[i] + u];
+            ++w;
+        }
+    }
+    out_ptr[n] = w;
+    free(cnt); free(gcol); free(glen); free(next);
+    return w;
+}
+
+/* ------------------------------------------------------------- seeds (O4.1) */
+
+/* SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): state += golden gamma, then
+ * the variant-13 finaliser of MurmurHash3 as published by Stafford. */
+static uint64_t splitmix64_next(uint64_t *state)
+{
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+uint64_t oracle_splitmix64(uint64_t *state) { return splitmix64_next(state); }
+
+/*
+ * The paper's "rand" seeds: n_seed distinct node ids drawn uniformly per query.
+ * Query q draws from one SplitMix64 stream whose state starts at
+ * global_seed + q * 2^32; a draw z maps to the id floor(z * n / 2^64), and an id
+ * already drawn is drawn again.  When 2 * n_seed > n the seeds are simply the
+ * ids 0 .. n_seed-1 (n_seed clipped to n).
+ */
+int oracle_seeds_random(uint64_t global_seed, int64_t nq, int64_t n, int n_seed, int32_t *out)
+{
+    if (n <= 0 || n_seed <= 0)
+        return ORACLE_E_INVAL;
+    int m = n_seed < n ? n_seed : (int)n;
+    for (int64_t q = 0; q < nq; ++q) {
+        int32_t *o = out + q * (int64_t)n_seed;
+        for (int t = m; t < n_seed; ++t)
+            o[t] = -1;
+        if (2 * (int64_t)m > n) {
+            for (int t = 0; t < m; ++t)
+                o[t] = t;
+            continue;
+        }
+        uint64_t st = global_seed + ((uint64_t)q << 32);
+        int got = 0;
+        while (got < m) {
+            uint64_t z = splitmix64_next(&st);
+            int32_t id = (int32_t)(((unsigned __int128)z * (uint64_t)n) >> 64);
+            int dup = 0;
+            for (int t = 0; t < got; ++t)
+                if (o[t] == id) {
+                    dup = 1;
+                    break;
+                }
+            if (!dup)
+                o[got++] = id;
+        }
+    }
+    return ORACLE_OK;
+}
+
+/*
+ * Pivot seed rule (stands in for the paper's vp-tree seeds, which reach nodes
+ * roughly near the query): the pivots are the P = min(n_pivot, n) base ids
+ * floor(t * n / P), t = 0..P-1; the seeds of a query are its n_seed nearest
+ * pivots in (distance, id) order.  out [nq, n_seed], -1 padded.
+ */
+int oracle_seeds_pivot(const float *X, int64_t n, int d, const float *Q, int64_t nq,
+                       int n_pivot, int n_seed, int32_t *out, int threads)
+{
+    if (n <= 0 || d <= 0 || n_pivot <= 0 || n_seed <= 0)
+        return ORACLE_E_INVAL;
+    int64_t P = n_pivot < n ? n_pivot : n;
+#ifdef _OPENMP
+    if (threads > 0)
+        omp_set_num_threads(threads);
+#pragma omp parallel
+#endif
+    {
+        double *dl = (double *)malloc((size_t)n_seed * sizeof(double));
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+        for (int64_t q = 0; q < nq; ++q) {
+            int32_t *il = out + q * (int64_t)n_seed;
+            int cnt = 0;
+            for (int64_t t = 0; t < P; ++t) {
+                int64_t id = t * n / P;
+                sorted_insert(dl, il, &cnt, n_seed, dist64(Q + q * (int64_t)d, X + id * (int64_t)d, d),
+                              (int32_t)id);
+            }
+            for (int t = cnt; t < n_seed; ++t)
+                il[t] = -1;
+        }
+        free(dl);
+    }
+    return ORACLE_OK;
+}
+
+/* ----------------------------------------------------------- search (O4) */
+
+/* The visited set C of Algorithms Set / IsSet: a table b of size
+ * s = 2^floor((floor(log2 n) + b) / 2), b = 11, hash h = i mod s (one bit mask);
+ * the first id of a bucket sits in b_h, later ones in the bucket's list L_h. */
+typedef struct {
+    int32_t *b;
+    int32_t **L;
+    int *Ln, *Lcap;
+    int64_t s;
+} visited_t;
+
+int64_t oracle_hash_size(int64_t n)
+{
+    int lg = 0;
+    while (((int64_t)1 << (lg + 1)) <= n)
+        ++lg; /* floor(log2 n) */
+    return (int64_t)1 << ((lg + 11) / 2);
+}
+
+static int visited_init(visited_t *v, int64_t n)
+{
+    v->s = oracle_hash_size(n);
+    v->b = (int32_t *)malloc((size_t)v->s * sizeof(int32_t));
+    v->L = (int32_t **)calloc((size_t)v->s, sizeof(int32_t *));
+    v->Ln = (int *)calloc((size_t)v->s, sizeof(int));
+    v->Lcap = (int *)calloc((size_t)v->s, sizeof(int));
+    if (!v->b || !v->L || !v->Ln || !v->Lcap)
+        return -1;
+    for (int64_t h = 0; h < v->s; ++h)
+        v->b[h] = -1; /* empty */
+    return 0;
+}
+
+static void visited_clear(visited_t *v)
+{
+    for (int64_t h = 0; h < v->s; ++h) {
+        v->b[h] = -1;
+        v->Ln[h] = 0;
+    }
+}
+
+static void visited_free(visited_t *v)
+{
+    for (int64_t h = 0; h < v->s; ++h)
+        free(v->L[h]);
+    free(v->L);
+    free(v->Ln);
+    free(v->Lcap);
+    free(v->b);
+}
+
+static void visited_set(visited_t *v, int32_t i) /* Algorithm Set */
+{
+    int64_t h = (int64_t)i & (v->s - 1);
+    if (v->b[h] == -1) {
+        v->b[h] = i;
+    } else if (v->b[h] != i) {
+        for (int t = 0; t < v->Ln[h]; ++t)
+            if (v->L[h][t] == i)
+                return;
+        if (v->Ln[h] == v->Lcap[h]) {
+            v->Lcap[h] = v->Lcap[h] ? 2 * v->Lcap[h] : 4;
+            v->L[h] = (int32_t *)realloc(v->L[h], (size_t)v->Lcap[h] * sizeof(int32_t));
+        }
+        v->L[h][v->Ln[h]++] = i;
+    }
+}
+
+static int visited_isset(const visited_t *v, int32_t i) /* Algorithm IsSet */
+{
+    int64_t h = (int64_t)i & (v->s - 1);
+    if (v->b[h] == i)
+        return 1;
+    for (int t = 0; t < v->Ln[h]; ++t)
+        if (v->L[h][t] == i)
+            return 1;
+    return 0;
+}
+
+typedef struct {
+    double d;
+    int32_t id;
+} cand_t;
+
+int oracle_hash_selftest(const int32_t *ids, int64_t m, int64_t n, uint8_t *was_set)
+{
+    visited_t v;
+    if (visited_init(&v, n))
+        return ORACLE_E_NOMEM;
+    for (int64_t t = 0; t < m; ++t) {
+        was_set[t] = (uint8_t)visited_isset(&v, ids[t]);
+        visited_set(&v, ids[t]);
+    }
+    visited_free(&v);
+    return ORACLE_OK;
+}
+
+/*
+ * Algorithm 1 (KnnSearch) for each query, over the graph (ptr, col) whose lists
+ * are ordered by length, with the readings the paper leaves open:
+ *  - the seeds are given explicitly (seeds[q, 0..n_seed), -1 entries ignored);
+ *    every seed is marked visited and its distance is computed and counted;
+ *    S starts as all seeds, R as the k nearest of them, r = +inf;
+ *  - argmin over S and argmax over R break ties by (distance, id);
+ *  - a neighbour n enters S if d(n,q) <= r(1+eps) and R if d(n,q) <= r; after an
+ *    insertion that leaves |R| = k, r = max over R; the search stops when the
+ *    popped s has d(s,q) > r(1+eps); eps = +inf means no bound;
+ *  - p counts every list entry scanned, visited or not, so exactly the first
+ *    min(e_s, degree) entries are read (e_s <= 0 means all).
+ * Output rows: R ordered by (distance, id), padded with -1 / +inf.
+ * stats [nq, 4]: distance computations, expansions (nodes popped and scanned),
+ * largest |S|, flags (0).
+ */
+int oracle_search(const int64_t *ptr, const int32_t *col, const float *X, int64_t n, int d,
+                  const float *Q, int64_t nq, int k, int e_s, double eps, const int32_t *seeds,
+                  int n_seed, int32_t *out_ids, double *out_dist, int64_t *stats, int threads)
+{
+    if (k <= 0 || d <= 0 || n <= 0 || n_seed <= 0)
+        return ORACLE_E_INVAL;
+    int64_t e_lim = e_s > 0 ? e_s : INT64_MAX;
+    int err = 0;
+#ifdef _OPENMP
+    if (threads > 0)
+        omp_set_num_threads(threads);
+#pragma omp parallel
+#endif
+    {
+        visited_t vis;
+        int ok = visited_init(&vis, n) == 0;
+        int64_t scap = 1024;
+        cand_t *S = (cand_t *)malloc((size_t)scap * sizeof(cand_t));
+        cand_t *R = (cand_t *)malloc((size_t)(k + 1) * sizeof(cand_t));
+        if (!ok || !S || !R) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            err = ORACLE_E_NOMEM;
+        }
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 8)
+#endif
+        for (int64_t qi = 0; qi < nq; ++qi) {
+            if (err)
+                continue;
+            const float *q = Q + qi * (int64_t)d;
+            visited_clear(&vis);
+            int64_t ns = 0, nr = 0, maxs = 0, ndc = 0, nexp = 0;
+            double r = INFINITY;
+            /* S <- Seed(G), R <- S (k nearest), C <- seeds */
+            for (int t = 0; t < n_seed; ++t) {
+                int32_t sd = seeds[qi * (int64_t)n_seed + t];
+                if (sd < 0 || sd >= n || visited_isset(&vis, sd))
+                    continue;
+                visited_set(&vis, sd);
+                double dv = dist64(q, X + (int64_t)sd * d, d);
+                ++ndc;
+                if (ns == scap) {
+                    scap *= 2;
+                    S = (cand_t *)realloc(S, (size_t)scap * sizeof(cand_t));
+                }
+                S[ns].d = dv;
+                S[ns].id = sd;
+                ++ns;
+            }
+            for (int64_t t = 0; t < ns; ++t) {
+                /* R keeps the k nearest seeds: insert, evict the largest when |R| > k */
+                R[nr++] = S[t];
+                if (nr > k) {
+                    int64_t a = 0;
+                    for (int64_t u = 1; u < nr; ++u)
+                        if (lt_pair(R[a].d, R[a].id, R[u].d, R[u].id))
+                            a = u;
+                    R[a] = R[--nr];
+                }
+            }
+            maxs = ns;
+            while (ns > 0) {
+                int64_t a = 0; /* s <- argmin_{x in S} d(x, q) */
+                for (int64_t u = 1; u < ns; ++u)
+                    if (lt_pair(S[u].d, S[u].id, S[a].d, S[a].id))
+                        a = u;
+                cand_t s = S[a];
+                S[a] = S[--ns];
+                double bound = isinf(eps) ? INFINITY : r * (1.0 + eps);
+                if (s.d > bound)
+                    break;
+                ++nexp;
+                int64_t p = 1;
+                for (int64_t t = ptr[s.id]; t < ptr[s.id + 1] && p <= e_lim; ++t, ++p) {
+                    int32_t nb = col[t];
+                    if (visited_isset(&vis, nb))
+                        continue;
+                    visited_set(&vis, nb);
+                    double dn = dist64(q, X + (int64_t)nb * d, d);
+                    ++ndc;
+                    bound = isinf(eps) ? INFINITY : r * (1.0 + eps);
+                    if (dn <= bound) {
+                        if (ns == scap) {
+                            scap *= 2;
+                            S = (cand_t *)realloc(S, (size_t)scap * sizeof(cand_t));
+                        }
+                        S[ns].d = dn;
+                        S[ns].id = nb;
+                        ++ns;
+                        if (ns > maxs)
+                            maxs = ns;
+                    }
+                    if (dn <= r) {
+                        R[nr].d = dn;
+                        R[nr].id = nb;
+                        ++nr;
+                        if (nr > k) {
+                            int64_t b = 0;
+                            for (int64_t u = 1; u < nr; ++u)
+                                if (lt_pair(R[b].d, R[b].id, R[u].d, R[u].id))
+                                    b = u;
+                            R[b] = R[--nr];
+                        }
+                        if (nr == k) {
+                            r = R[0].d;
+                            for (int64_t u = 1; u < nr; ++u)
+                                if (R[u].d > r)
+                                    r = R[u].d;
+                        }
+                    }
+                }
+            }
+            /* output R ordered by (distance, id) */
+            for (int64_t u = 1; u < nr; ++u) {
+                cand_t x = R[u];
+                int64_t v = u;
+                while (v > 0 && lt_pair(x.d, x.id, R[v - 1].d, R[v - 1].id)) {
+                    R[v] = R[v - 1];
+                    --v;
+                }
+                R[v] = x;
+            }
+            for (int t = 0; t < k; ++t) {
+                out_ids[qi * k + t] = t < nr ? R[t].id : -1;
+                out_dist[qi * k + t] = t < nr ? R[t].d : INFINITY;
+            }
+            if (stats) {
+                stats[qi * 4 + 0] = ndc;
+                stats[qi * 4 + 1] = nexp;
+                stats[qi * 4 + 2] = maxs;
+                stats[qi * 4 + 3] = 0;
+            }
+        }
+        free(S);
+        free(R);
+        if (ok)
+            visited_free(&vis);
+    }
+    return err;
+}
+
+/* ------------------------------------------------------- reduced precision (O5) */
+
+/* bfloat16 round-to-nearest-even of a float32, returned widened to float32 */
+static float bf16_round1(float x)
+{
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u && (u & 0x007FFFFFu)) {
+        u |= 0x00400000u; /* quiet NaN */
+    } else {
+        uint32_t lsb = (u >> 16) & 1u;
+        u += 0x7FFFu + lsb;
+    }
+    u &= 0xFFFF0000u;
+    float y;
+    memcpy(&y, &u, 4);
+    return y;
+}
+
+void oracle_bf16_round(const float *x, int64_t m, float *y)
+{
+    for (int64_t t = 0; t < m; ++t)
+        y[t] = bf16_round1(x[t]);
+}
+
+/* ------------------------------------------------------------- MLP (O6) */
+
+/*
+ * The per-query parameter predictor: 16 -> 64 -> 64 -> 2 with ReLU after the two
+ * hidden layers.  Parameters are one flat vector in the order
+ *   W1[64][16], b1[64], W2[64][64], b2[64], W3[2][64], b3[2]   (5,378 values).
+ * Loss: mean over the batch of 0.5 * sum_o (y_o - t_o)^2.
+ */
+#define MLP_I 16
+#define MLP_H 64
+#define MLP_O 2
+#define MLP_NPARAM (MLP_H * MLP_I + MLP_H + MLP_H * MLP_H + MLP_H + MLP_O * MLP_H + MLP_O)
+
+int oracle_mlp_nparam(void) { return MLP_NPARAM; }
+
+static void mlp_views(const double *P, const double **W1, const double **b1, const double **W2,
+                      const double **b2, const double **W3, const double **b3)
+{
+    *W1 = P;
+    *b1 = *W1 + MLP_H * MLP_I;
+    *W2 = *b1 + MLP_H;
+    *b2 = *W2 + MLP_H * MLP_H;
+    *W3 = *b2 + MLP_H;
+    *b3 = *W3 + MLP_O * MLP_H;
+}
+
+/* forward pass; y [B, 2] */
+void oracle_mlp_forward(const double *P, const double *x, int64_t B, double *y)
+{
+    const double *W1, *b1, *W2, *b2, *W3, *b3;
+    mlp_views(P, &W1, &b1, &W2, &b2, &W3, &b3);
+    for (int64_t b = 0; b < B; ++b) {
+        double h1[MLP_H], h2[MLP_H];
+        for (int o = 0; o < MLP_H; ++o) {
+            double s = b1[o];
+            for (int i = 0; i < MLP_I; ++i)
+                s += W1[o * MLP_I + i] * x[b * MLP_I + i];
+            h1[o] = s > 0 ? s : 0;
+        }
+        for (int o = 0; o < MLP_H; ++o) {
+            double s = b2[o];
+            for (int i = 0; i < MLP_H; ++i)
+                s += W2[o * MLP_H + i] * h1[i];
+            h2[o] = s > 0 ? s : 0;
+        }
+        for (int o = 0; o < MLP_O; ++o) {
+            double s = b3[o];
+            for (int i = 0; i < MLP_H; ++i)
+                s += W3[o * MLP_H + i] * h2[i];
+            y[b * MLP_O + o] = s;
+        }
+    }
+}
+
+/* loss and its gradient with respect to every parameter (G has MLP_NPARAM entries) */
+double oracle_mlp_loss_grad(const double *P, const double *x, const double *t, int64_t B, double *G)
+{
+    const double *W1, *b1, *W2, *b2, *W3, *b3;
+    mlp_views(P, &W1, &b1, &W2, &b2, &W3, &b3);
+    double *gW1 = G, *gb1 = gW1 + MLP_H * MLP_I, *gW2 = gb1 + MLP_H, *gb2 = gW2 + MLP_H * MLP_H;
+    double *gW3 = gb2 + MLP_H, *gb3 = gW3 + MLP_O * MLP_H;
+    memset(G, 0, sizeof(double) * MLP_NPARAM);
+    double loss = 0;
+    for (int64_t b = 0; b < B; ++b) {
+        double a1[MLP_H], h1[MLP_H], a2[MLP_H], h2[MLP_H], y[MLP_O];
+        const double *xb = x + b * MLP_I;
+        for (int o = 0; o < MLP_H; ++o) {
+            double s = b1[o];
+            for (int i = 0; i < MLP_I; ++i)
+                s += W1[o * MLP_I + i] * xb[i];
+            a1[o] = s;
+            h1[o] = s > 0 ? s : 0;
+        }
+        for (int o = 0; o < MLP_H; ++o) {
+            double s = b2[o];
+            for (int i = 0; i < MLP_H; ++i)
+                s += W2[o * MLP_H + i] * h1[i];
+            a2[o] = s;
+            h2[o] = s > 0 ? s : 0;
+        }
+        double dy[MLP_O];
+        for (int o = 0; o < MLP_O; ++o) {
+            double s = b3[o];
+            for (int i = 0; i < MLP_H; ++i)
+                s += W3[o * MLP_H + i] * h2[i];
+            y[o] = s;
+            double e = y[o] - t[b * MLP_O + o];
+            loss += 0.5 * e * e;
+            dy[o] = e / (double)B;
+        }
+        double dh2[MLP_H], dh1[MLP_H];
+        for (int i = 0; i < MLP_H; ++i)
+            dh2[i] = 0;
+        for (int o = 0; o < MLP_O; ++o) {
+            gb3[o] += dy[o];
+            for (int i = 0; i < MLP_H; ++i) {
+                gW3[o * MLP_H + i] += dy[o] * h2[i];
+                dh2[i] += W3[o * MLP_H + i] * dy[o];
+            }
+        }
+        for (int i = 0; i < MLP_H; ++i)
+            dh1[i] = 0;
+        for (int o = 0; o < MLP_H; ++o) {
+            double da = a2[o] > 0 ? dh2[o] : 0;
+            gb2[o] += da;
+            for (int i = 0; i < MLP_H; ++i) {
+                gW2[o * MLP_H + i] += da * h1[i];
+                dh1[i] += W2[o * MLP_H + i] * da;
+            }
+        }
+        for (int o = 0; o < MLP_H; ++o) {
+            double da = a1[o] > 0 ? dh1[o] : 0;
+            gb1[o] += da;
+            for (int i = 0; i < MLP_I; ++i)
+                gW1[o * MLP_I + i] += da * xb[i];
+        }
+    }
+    return loss / (double)B;
+}
+
+/* One Adam step (Kingma & Ba 2015, Algorithm 1) on P with moments m, v at step
+ * count t >= 1. */
+void oracle_adam_step(double *P, const double *G, double *m, double *v, int64_t np, int64_t t,
+                      double lr, double beta1, double beta2, double eps)
+{
+    double c1 = 1.0 - pow(beta1, (double)t), c2 = 1.0 - pow(beta2, (double)t);
+    for (int64_t i = 0; i < np; ++i) {
+        m[i] = beta1 * m[i] + (1.0 - beta1) * G[i];
+        v[i] = beta2 * v[i] + (1.0 - beta2) * G[i] * G[i];
+        double mh = m[i] / c1, vh = v[i] / c2;
+        P[i] -= lr * mh / (sqrt(vh) + eps);
+    }
+}

@@ -1,0 +1,145 @@
+"""Pins of the oracle's exact kNN graph and static degree adjustment (Algorithm 2).
+
+Each check compares against something other than the oracle itself: scipy's
+k-d tree, hand-built point sets, scipy.sparse transposes for the special graphs
+KNNG / TKNNG / BKNNG of Sec. 2.1, and a sequential transcription of Algorithm 2.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.spatial import cKDTree
+
+from paper_1810_07355_gb300 import synth
+
+
+def test_knn_matches_kdtree(oracle_lib):
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=(600, 8)).astype(np.float32)
+    Q = rng.normal(size=(40, 8)).astype(np.float32)
+    ids, dist = oracle_lib.knn(X, Q, 12)
+    td, ti = cKDTree(X.astype(np.float64)).query(Q.astype(np.float64), k=12)
+    assert np.array_equal(ids, ti)
+    np.testing.assert_allclose(dist, td, rtol=1e-12)
+
+
+def test_knng_excludes_self_matches_kdtree(oracle_lib):
+    X = synth.gaussian_mixture(500, d=16, components=5, sigma=3.0, seed=11)
+    ids, dist = oracle_lib.knng(X, 10)
+    td, ti = cKDTree(X.astype(np.float64)).query(X.astype(np.float64), k=11)
+    # continuous data: the nearest point of every row is itself
+    assert np.array_equal(ti[:, 0], np.arange(500))
+    assert np.array_equal(ids, ti[:, 1:])
+    np.testing.assert_allclose(dist, td[:, 1:], rtol=1e-12)
+
+
+def test_knn_line_ties_and_duplicates(oracle_lib):
+    # points on a line: 0, 1, 2, 2 (duplicate), 5
+    X = np.array([[0], [1], [2], [2], [5]], np.float32)
+    ids, dist = oracle_lib.knng(X, 3)
+    # node 1: nodes 0, 2, 3 all at distance 1 -> id order
+    assert ids[1].tolist() == [0, 2, 3]
+    # node 2: its duplicate 3 at distance 0 is a neighbour (self excluded by id only)
+    assert ids[2].tolist() == [3, 1, 0]
+    assert dist[2].tolist() == [0.0, 1.0, 2.0]
+    assert ids[4].tolist() == [2, 3, 1]
+    # k larger than n - 1 pads with -1 / inf
+    ids, dist = oracle_lib.knng(X[:3], 4)
+    assert ids[0].tolist() == [1, 2, -1, -1]
+    assert np.isinf(dist[0, 2:]).all()
+
+
+def _csr(ptr, col, ln, n):
+    return sp.csr_matrix((ln, col, ptr), shape=(n, n))
+
+
+def _knng_matrix(ids, dist, m):
+    n = ids.shape[0]
+    rows = np.repeat(np.arange(n), m)
+    return sp.csr_matrix((dist[:, :m].ravel(), (rows, ids[:, :m].ravel())), shape=(n, n))
+
+
+def _check_sorted_unique(ptr, col, ln):
+    for i in range(len(ptr) - 1):
+        c, l = col[ptr[i]:ptr[i + 1]], ln[ptr[i]:ptr[i + 1]]
+        assert len(set(c.tolist())) == len(c), "duplicate edge"
+        assert i not in set(c.tolist()), "self loop"
+        order = np.lexsort((c, l))
+        assert np.array_equal(order, np.arange(len(c))), "not sorted by (len, id)"
+
+
+@pytest.fixture(scope="module")
+def small_graph(oracle_lib):
+    X = synth.gaussian_mixture(300, d=12, components=4, sigma=4.0, seed=5)
+    ids, dist = oracle_lib.knng(X, 16)
+    return X, ids, dist
+
+
+def test_degree_knng_special_case(oracle_lib, small_graph):
+    _, ids, dist = small_graph
+    ptr, col, ln = oracle_lib.adjust_degree(ids, dist, 10, 0)
+    assert np.array_equal(np.diff(ptr), np.full(300, 10))
+    assert np.array_equal(col.reshape(300, 10), ids[:, :10])
+    np.testing.assert_array_equal(ln.reshape(300, 10), dist[:, :10])
+
+
+def test_degree_tknng_is_transpose(oracle_lib, small_graph):
+    _, ids, dist = small_graph
+    n, k = ids.shape
+    ptr, col, ln = oracle_lib.adjust_degree(ids, dist, 0, k)
+    got = _csr(ptr, col, ln, n)
+    want = _knng_matrix(ids, dist, k).T.tocsr()
+    assert (got != want).nnz == 0
+    _check_sorted_unique(ptr, col, ln)
+
+
+def test_degree_bknng_is_union(oracle_lib, small_graph):
+    _, ids, dist = small_graph
+    n, k = ids.shape
+    h = k // 2
+    ptr, col, ln = oracle_lib.adjust_degree(ids, dist, h, h)
+    A = _knng_matrix(ids, dist, h)
+    want = A.maximum(A.T).tocsr()  # symmetric distances: same value either way
+    got = _csr(ptr, col, ln, n)
+    assert (got != want).nnz == 0
+    _check_sorted_unique(ptr, col, ln)
+
+
+def _alg2_sequential(ids, dist, e_o, e_i):
+    """Algorithm 2 walked node by node with loop bound p <= max(e_o, e_i)."""
+    n, k = ids.shape
+    adj = [dict() for _ in range(n)]
+    for o in range(n):
+        for p in range(1, min(k, max(e_o, e_i)) + 1):
+            nb, ln = int(ids[o, p - 1]), float(dist[o, p - 1])
+            if p <= e_o:
+                adj[o][nb] = ln  # a forward edge keeps its own length
+            if p <= e_i and o not in adj[nb]:
+                adj[nb][o] = ln
+    return adj
+
+
+@pytest.mark.parametrize("e_o,e_i", [(3, 7), (8, 2), (5, 5), (16, 16), (0, 4)])
+def test_degree_matches_sequential_alg2(oracle_lib, small_graph, e_o, e_i):
+    _, ids, dist = small_graph
+    n, k = ids.shape
+    ptr, col, ln = oracle_lib.adjust_degree(ids, dist, e_o, e_i)
+    adj = _alg2_sequential(ids, dist, e_o, e_i)
+    for o in range(n):
+        got = dict(zip(col[ptr[o]:ptr[o + 1]].tolist(), ln[ptr[o]:ptr[o + 1]].tolist()))
+        assert got == adj[o]
+    _check_sorted_unique(ptr, col, ln)
+    outdeg = np.diff(ptr)
+    indeg = np.bincount(col, minlength=n)
+    assert (outdeg >= min(e_o, k)).all()
+    assert (indeg >= min(e_i, k)).all()
+
+
+def test_degree_row_subset(oracle_lib, small_graph):
+    _, ids, dist = small_graph
+    full = oracle_lib.adjust_degree(ids, dist, 6, 9)
+    rows = np.array([299, 0, 17, 150])
+    ptr, col, ln = oracle_lib.adjust_degree(ids, dist, 6, 9, rows=rows)
+    for r, i in enumerate(rows):
+        a = full[1][full[0][i]:full[0][i + 1]]
+        b = col[ptr[r]:ptr[r + 1]]
+        assert np.array_equal(a, b)

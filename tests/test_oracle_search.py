@@ -1,0 +1,213 @@
+"""Pins of the oracle's KnnSearch (Algorithm 1), visited set (Set / IsSet), seed
+rules, bfloat16 rounding and the predictor network.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.sparse.csgraph import connected_components
+from scipy.spatial import cKDTree
+
+from paper_1810_07355_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_chain_trace(oracle_lib):
+    g = json.load(open(os.path.join(GOLDEN, "chain_search.json")))
+    X = np.array(g["X"], np.float32)
+    n = len(X)
+    rows = [[c for c in (i - 1, i + 1) if 0 <= c < n] for i in range(n)]
+    ptr = np.cumsum([0] + [len(r) for r in rows]).astype(np.int64)
+    col = np.array(sum(rows, []), np.int32)
+    Q = np.array([g["query"]], np.float32)
+    seeds = np.array([g["seeds"]], np.int32)
+    for c in g["cases"]:
+        ids, dist, st = oracle_lib.search(ptr, col, X, Q, g["k"], c["e_s"], g["eps"], seeds)
+        assert ids[0].tolist() == c["ids"]
+        np.testing.assert_allclose(dist[0], c["dist"], rtol=1e-6)
+        assert st[0, 0] == c["distance_computations"]
+        assert st[0, 1] == c["expansions"]
+
+
+@pytest.fixture(scope="module")
+def one_cluster(oracle_lib):
+    X = synth.gaussian_mixture(800, d=16, components=1, sigma=5.0, seed=31)
+    Q = synth.gaussian_mixture(30, d=16, components=1, sigma=5.0, seed=32)
+    ids, dist = oracle_lib.knng(X, 12)
+    ptr, col, ln = oracle_lib.adjust_degree(ids, dist, 6, 12)
+    return X, Q, (ptr, col, ln)
+
+
+def test_unbounded_search_is_exact(oracle_lib, one_cluster):
+    """eps = inf and e_s = inf on a strongly connected graph visit every node."""
+    X, Q, (ptr, col, _) = one_cluster
+    n = len(X)
+    A = sp.csr_matrix((np.ones(len(col)), col, ptr), shape=(n, n))
+    assert connected_components(A, directed=True, connection="strong")[0] == 1
+    seeds = oracle_lib.seeds_random(5, len(Q), n, 3)
+    ids, dist, st = oracle_lib.search(ptr, col, X, Q, 10, 0, np.inf, seeds)
+    td, ti = cKDTree(X.astype(np.float64)).query(Q.astype(np.float64), k=10)
+    assert np.array_equal(ids, ti)
+    np.testing.assert_allclose(dist, td, rtol=1e-12)
+    assert (st[:, 0] == n).all()
+
+
+def test_complete_graph_is_exact(oracle_lib):
+    rng = np.random.default_rng(8)
+    X = rng.normal(size=(60, 5)).astype(np.float32)
+    Q = rng.normal(size=(10, 5)).astype(np.float32)
+    n = len(X)
+    col = np.concatenate([[j for j in range(n) if j != i] for i in range(n)]).astype(np.int32)
+    ptr = np.arange(0, n * (n - 1) + 1, n - 1, dtype=np.int64)
+    seeds = np.zeros((len(Q), 1), np.int32)
+    ids, dist, _ = oracle_lib.search(ptr, col, X, Q, 7, 0, 0.0, seeds)
+    td, ti = cKDTree(X.astype(np.float64)).query(Q.astype(np.float64), k=7)
+    assert np.array_equal(ids, ti)
+
+
+def test_results_are_valid(oracle_lib, one_cluster):
+    X, Q, (ptr, col, _) = one_cluster
+    seeds = oracle_lib.seeds_random(9, len(Q), len(X), 4)
+    for eps in (0.0, 0.05):
+        ids, dist, st = oracle_lib.search(ptr, col, X, Q, 10, 4, eps, seeds)
+        for q in range(len(Q)):
+            got = ids[q][ids[q] >= 0]
+            assert len(set(got.tolist())) == len(got)
+            rec = np.linalg.norm(X[got].astype(np.float64) - Q[q].astype(np.float64), axis=1)
+            np.testing.assert_allclose(dist[q][:len(got)], rec, rtol=1e-12)
+            assert (np.diff(dist[q][:len(got)]) >= 0).all()
+        assert (st[:, 0] >= st[:, 1]).all()
+
+
+def test_small_k_pads(oracle_lib):
+    X = np.array([[0.0], [1.0], [5.0]], np.float32)
+    ptr = np.array([0, 1, 2, 2], np.int64)
+    col = np.array([1, 0], np.int32)
+    ids, dist, _ = oracle_lib.search(ptr, col, X, np.array([[0.2]], np.float32), 3, 0, 0.0,
+                                     np.array([[0]], np.int32))
+    assert ids[0].tolist() == [0, 1, -1] and np.isinf(dist[0, 2])
+
+
+def test_recall_grows_with_eps(oracle_lib):
+    X, Q = synth.workload("gmm10k", n=4000, nq=100)
+    ids, dist = oracle_lib.knng(X, 40)
+    g = oracle_lib.adjust_path(*oracle_lib.adjust_degree(ids, dist, 10, 30))
+    seeds = oracle_lib.seeds_pivot(X, Q, 1024, 10)
+    gt, _ = oracle_lib.knn(X, Q, 10)
+    rec = []
+    for eps in (0.0, 0.02, 0.05, 0.1, 0.2):
+        r, _, _ = oracle_lib.search(g[0], g[1], X, Q, 10, 10, eps, seeds)
+        rec.append(np.mean([len(set(a) & set(b)) / 10 for a, b in zip(r, gt)]))
+    assert all(b >= a - 0.01 for a, b in zip(rec, rec[1:]))
+    assert rec[-1] > 0.9
+
+
+def test_hash_size_formula(oracle_lib):
+    # s = 2^floor((floor(log2 n) + 11) / 2)
+    assert oracle_lib.hash_size(10_000) == 4096
+    assert oracle_lib.hash_size(1_000_000) == 32768
+    assert oracle_lib.hash_size(1_200_000) == 32768
+    assert oracle_lib.hash_size(1 << 20) == 1 << 15
+    assert oracle_lib.hash_size(2) == 1 << 6
+
+
+def test_hash_set_isset_is_a_set(oracle_lib):
+    rng = np.random.default_rng(4)
+    n = 10_000  # s = 4096: plenty of collisions in 20k draws from 2^20 ids
+    ids = rng.integers(0, 1 << 20, size=20_000).astype(np.int32)
+    got = oracle_lib.hash_selftest(ids, n)
+    seen, want = set(), []
+    for i in ids.tolist():
+        want.append(i in seen)
+        seen.add(i)
+    assert got.tolist() == want
+
+
+def test_splitmix64_published_vectors(oracle_lib):
+    g = json.load(open(os.path.join(GOLDEN, "splitmix64.json")))
+    for v in g["vectors"]:
+        assert oracle_lib.splitmix64(v["state"], len(v["outputs"])) == [int(x, 0) for x in v["outputs"]]
+
+
+def test_random_seeds_properties(oracle_lib):
+    s = oracle_lib.seeds_random(123, 4000, 1000, 10)
+    assert s.min() >= 0 and s.max() < 1000
+    assert all(len(set(r.tolist())) == 10 for r in s)
+    counts = np.bincount(s.ravel(), minlength=1000)
+    chi2 = ((counts - 40.0) ** 2 / 40.0).sum()
+    assert chi2 < 1000 + 6 * np.sqrt(2000)  # df = 999
+    assert not np.array_equal(s[0], s[1])
+    assert np.array_equal(oracle_lib.seeds_random(123, 4000, 1000, 10), s)
+    assert oracle_lib.seeds_random(1, 2, 5, 3).tolist() == [[0, 1, 2], [0, 1, 2]]
+
+
+def test_pivot_seeds_match_kdtree(oracle_lib):
+    rng = np.random.default_rng(6)
+    X = rng.normal(size=(5000, 6)).astype(np.float32)
+    Q = rng.normal(size=(50, 6)).astype(np.float32)
+    s = oracle_lib.seeds_pivot(X, Q, 256, 5)
+    piv = (np.arange(256) * 5000) // 256
+    _, ti = cKDTree(X[piv].astype(np.float64)).query(Q.astype(np.float64), k=5)
+    assert np.array_equal(s, piv[ti])
+
+
+def test_bf16_round_matches_torch(oracle_lib):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(2)
+    x = np.concatenate([rng.normal(size=5000) * 10 ** rng.uniform(-30, 30, 5000),
+                        np.arange(-300, 300), [0.0, -0.0, np.inf, -np.inf]]).astype(np.float32)
+    want = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    assert np.array_equal(oracle_lib.bf16_round(x), want)
+    # integers 0..256 are exact in bfloat16
+    ints = np.arange(0, 257, dtype=np.float32)
+    assert np.array_equal(oracle_lib.bf16_round(ints), ints)
+
+
+def test_mlp_forward_matches_torch(oracle_lib):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(1)
+    P = rng.normal(size=oracle_lib.MLP_NPARAM) * 0.3
+    x = rng.normal(size=(17, 16))
+    sizes = [64 * 16, 64, 64 * 64, 64, 2 * 64, 2]
+    W1, b1, W2, b2, W3, b3 = [torch.from_numpy(a) for a in np.split(P, np.cumsum(sizes)[:-1])]
+    h = torch.relu(torch.from_numpy(x) @ W1.reshape(64, 16).T + b1)
+    h = torch.relu(h @ W2.reshape(64, 64).T + b2)
+    y = h @ W3.reshape(2, 64).T + b3
+    np.testing.assert_allclose(oracle_lib.mlp_forward(P, x), y.numpy(), rtol=1e-12, atol=1e-12)
+
+
+def test_mlp_gradient_finite_difference(oracle_lib):
+    rng = np.random.default_rng(9)
+    P = rng.normal(size=oracle_lib.MLP_NPARAM) * 0.3
+    x = rng.normal(size=(9, 16))
+    t = rng.normal(size=(9, 2))
+    loss, G = oracle_lib.mlp_loss_grad(P, x, t)
+    h = 1e-6
+    idx = rng.choice(oracle_lib.MLP_NPARAM, size=300, replace=False)
+    idx = np.concatenate([idx, np.arange(oracle_lib.MLP_NPARAM - 130, oracle_lib.MLP_NPARAM)])
+    for i in idx:
+        Pp, Pm = P.copy(), P.copy()
+        Pp[i] += h
+        Pm[i] -= h
+        fd = (oracle_lib.mlp_loss_grad(Pp, x, t)[0] - oracle_lib.mlp_loss_grad(Pm, x, t)[0]) / (2 * h)
+        assert abs(fd - G[i]) <= 1e-6 * max(1.0, abs(G[i])), (i, fd, G[i])
+    y = oracle_lib.mlp_forward(P, x)
+    assert abs(loss - 0.5 * ((y - t) ** 2).sum() / 9) < 1e-12
+
+
+def test_adam_matches_torch(oracle_lib):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(12)
+    P = rng.normal(size=50)
+    m, v = np.zeros(50), np.zeros(50)
+    tp = torch.nn.Parameter(torch.from_numpy(P.copy()))
+    opt = torch.optim.Adam([tp], lr=0.01)
+    for t in range(1, 6):
+        G = rng.normal(size=50)
+        oracle_lib.adam_step(P, G, m, v, t, 0.01)
+        tp.grad = torch.from_numpy(G)
+        opt.step()
+    np.testing.assert_allclose(P, tp.detach().numpy(), rtol=1e-12, atol=1e-14)
