@@ -1,0 +1,178 @@
+/*
+ * onng — GB300 (sm_103a) library for degree- and path-adjusted k-nearest-neighbour
+ * graph search, after Iwasaki & Miyazaki, "Optimization of Indexing Based on
+ * k-Nearest Neighbor Graph for Proximity Search in High-dimensional Data"
+ * (arXiv 1810.07355).
+ *
+ * Conventions shared by every entry point:
+ *  - All array pointers are DEVICE pointers owned by the caller.  The library
+ *    never frees them and keeps no reference to them after the call returns.
+ *    Float arrays must be 16-byte aligned (they are read with 16-byte loads).
+ *  - Matrices are row-major.  Vectors X [n, d] and queries Q [nq, d] are float32
+ *    with d a multiple of 4 (ONNG_E_UNSUPPORTED otherwise).
+ *  - Graphs are CSR: row_ptr [n+1] int64, col [nnz] int32, len [nnz] float32,
+ *    every row ordered by (length, id) ascending.  Lengths are Euclidean.
+ *  - `ws` / `ws_bytes` is caller-owned device scratch; each call that needs it
+ *    has a *_workspace_bytes query.  Too small a workspace gives ONNG_E_WORKSPACE.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) unless the comment says the call synchronises.
+ *  - Every call returns an onng_status; on failure onng_last_error() gives a
+ *    message (thread-local, valid until the next call on that thread).
+ *    Per-query soft failures are flags in the search stats, not call failures.
+ */
+#ifndef ONNG_H
+#define ONNG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *onng_stream_t; /* = cudaStream_t */
+
+enum onng_status {
+    ONNG_OK = 0,
+    ONNG_E_INVAL = 1,       /* bad argument (negative size, k > n - 1, NULL pointer ...) */
+    ONNG_E_WORKSPACE = 2,   /* ws_bytes smaller than the *_workspace_bytes query */
+    ONNG_E_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+    ONNG_E_LIMIT = 4,       /* an iteration cap was reached */
+    ONNG_E_UNSUPPORTED = 5  /* shape outside what the kernels handle (d % 4, k > 128 ...) */
+};
+
+/* per-query flags, stats[q*4 + 3] */
+#define ONNG_FLAG_S_OVERFLOW 1u      /* candidate pool full: farthest candidates dropped */
+#define ONNG_FLAG_VISIT_OVERFLOW 2u  /* visited set full: nodes may be re-evaluated */
+#define ONNG_FLAG_LIMIT 4u           /* max_expansions reached */
+
+const char *onng_last_error(void);
+int onng_version(void);
+
+/* ------------------------------------------------------------------ kNN graph
+ * Exact k nearest neighbours (the exact graph stands in for the approximate
+ * kNN graph the paper derives from an ANNG, Sec. 2.5 / Algorithm ConstructGraph).
+ *
+ * onng_knn: for every query row r < nq, the k base points of X [n, d] nearest to
+ * Q[r], as ids nbr [nq, k] int32 and Euclidean lengths len [nq, k] float32,
+ * ordered by (length, id).  If self_offset >= 0, query row r is base point
+ * self_offset + r and that id is excluded (a duplicate point with another id is
+ * still a neighbour).  k <= 256.  Rows with fewer than k candidates are padded
+ * with -1 / +inf.  Distances are ranked in float32 and the k survivors are
+ * rescored by direct difference; integer-valued inputs with squared norms
+ * below 2^23 are ranked exactly.
+ *
+ * onng_build_knng(X, n, d, k, ...) == onng_knn(X, n, d, X, n, k, 0, ...).
+ */
+size_t onng_knn_workspace_bytes(int64_t n, int32_t d, int64_t nq, int32_t k);
+int onng_knn(const float *X, int64_t n, int32_t d, const float *Q, int64_t nq, int32_t k,
+             int64_t self_offset, int32_t *nbr, float *len, void *ws, size_t ws_bytes,
+             onng_stream_t stream);
+int onng_build_knng(const float *X, int64_t n, int32_t d, int32_t k, int32_t *nbr, float *len,
+                    void *ws, size_t ws_bytes, onng_stream_t stream);
+
+/* ---------------------------------------------------- static degree adjustment
+ * Algorithm 2 (ConstructAdjustedGraph), set form: the adjusted list of node o is
+ *   first_{e_o}(N_k(o))  united with  { x : o in first_{e_i}(N_k(x)) },
+ * the loop bound of Algorithm 2 read as p <= max(e_o, e_i).  A reversed edge
+ * x->o carries the length stored for o->x; a forward edge keeps its own length
+ * when both directions exist.  Rows are ordered by (length, id).
+ * Input: the kNN lists nbr / len [n, k] of onng_build_knng.
+ *
+ * onng_adjust_degree_count writes the exact row_ptr [n+1] of the result and,
+ * if nnz_host != NULL, synchronises `stream` and stores the edge count there.
+ * onng_adjust_degree then fills col / len_out [nnz] using that row_ptr.
+ */
+size_t onng_adjust_degree_workspace_bytes(int64_t n, int32_t k);
+int onng_adjust_degree_count(const int32_t *nbr, const float *len, int64_t n, int32_t k,
+                             int32_t e_o, int32_t e_i, int64_t *row_ptr, int64_t *nnz_host,
+                             void *ws, size_t ws_bytes, onng_stream_t stream);
+int onng_adjust_degree(const int32_t *nbr, const float *len, int64_t n, int32_t k, int32_t e_o,
+                       int32_t e_i, const int64_t *row_ptr, int32_t *col, float *len_out,
+                       void *ws, size_t ws_bytes, onng_stream_t stream);
+
+/* ------------------------------------------------------------ path adjustment
+ * Algorithms 4/5 (AdjustPath / HasPath) read order-free: edge (i, j) is dropped
+ * when the INPUT graph has i->m and m->j with len(i,m) < len(i,j) and
+ * len(m,j) < len(i,j) (stored float32 lengths, strict comparisons).  Kept edges
+ * keep their order.  Outputs: row_ptr_out [n+1]; col_out / len_out need room for
+ * the input edge count.  If nnz_host != NULL the call synchronises and stores
+ * the kept edge count there.  removed_by (optional, [nnz_in] int32) receives, for
+ * every input edge, the smallest-position witness m or -1.
+ */
+size_t onng_adjust_path_workspace_bytes(int64_t n, int64_t nnz);
+int onng_adjust_path(const int64_t *row_ptr, const int32_t *col, const float *len, int64_t n,
+                     int64_t *row_ptr_out, int32_t *col_out, float *len_out, int64_t *nnz_host,
+                     int32_t *removed_by, void *ws, size_t ws_bytes, onng_stream_t stream);
+
+/* ---------------------------------------------------------------------- seeds
+ * onng_seeds_random: the paper's random seeds (Sec. 3): n_seed distinct ids per
+ * query, query q drawing from the SplitMix64 stream that starts at state
+ * global_seed + q * 2^32; a draw z maps to floor(z * n / 2^64), repeats are
+ * redrawn.  When 2 * n_seed > n the seeds are 0 .. n_seed-1.  out [nq, n_seed].
+ *
+ * onng_seeds_pivot: the n_seed nearest (distance, id) of the P = min(n_pivot, n)
+ * pivots floor(t * n / P); stands in for the paper's vp-tree seeds (Sec. 2,
+ * Table 5), which reach nodes roughly near the query.  n_seed <= 64.
+ */
+int onng_seeds_random(uint64_t global_seed, int64_t nq, int64_t n, int32_t n_seed, int32_t *out,
+                      onng_stream_t stream);
+size_t onng_seeds_pivot_workspace_bytes(int64_t n, int32_t d, int32_t n_pivot);
+int onng_seeds_pivot(const float *X, int64_t n, int32_t d, const float *Q, int64_t nq,
+                     int32_t n_pivot, int32_t n_seed, int32_t *out, void *ws, size_t ws_bytes,
+                     onng_stream_t stream);
+
+/* --------------------------------------------------------------------- search
+ * KnnSearch, Algorithm 1, one warp per query, with e_p (Eq. 1) given as e_s:
+ * best-first expansion from the seeds; only the first min(e_s, degree) list
+ * entries of an expanded node are scanned (e_s <= 0: all); a neighbour joins
+ * the candidates if d <= r(1+eps) and the results if d <= r; the search ends
+ * when the nearest candidate lies beyond r(1+eps).  Seeds are marked visited
+ * and counted; R starts as the k nearest seeds with r = +inf until an insertion
+ * fills R.  Ties break by (distance, id).  eps = +inf is allowed.
+ *
+ * The index: row_ptr / col as above (lengths are not needed by the search), X
+ * float32 [n, d]; X_bf16 [n, d] (bfloat16 bits, optional) is used when
+ * precision == ONNG_PREC_BF16, in which case the final list of k_rerank >= k
+ * candidates is rescored in float32 against X and the best k are returned.
+ *
+ * Outputs: out_ids [nq, k] int32 and out_dist [nq, k] float32 (Euclidean), sorted
+ * by (distance, id), padded -1 / +inf; stats [nq, 4] int32 (optional):
+ * distance computations, expansions, visited-set size, ONNG_FLAG_* bits.
+ * eps_q / es_q (optional, [nq]) override eps / e_s per query.
+ * Limits: k, k_rerank <= 128, n_seed <= 64, d <= 1024.
+ */
+enum onng_precision { ONNG_PREC_FP32 = 0, ONNG_PREC_BF16 = 1 };
+
+typedef struct {
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const float *X;
+    const uint16_t *X_bf16;
+    int64_t n;
+    int32_t d;
+    int32_t pad_;
+} onng_index;
+
+typedef struct {
+    int32_t k;
+    int32_t e_s;
+    float eps;
+    int32_t precision;
+    int32_t k_rerank;        /* bf16 only: candidates rescored in float32 (>= k) */
+    int32_t max_expansions;  /* 0: no cap; else per-query cap -> ONNG_FLAG_LIMIT */
+} onng_search_params;
+
+size_t onng_search_workspace_bytes(int64_t nq, const onng_index *idx, const onng_search_params *p);
+int onng_search(const onng_index *idx, const float *Q, int64_t nq, const onng_search_params *p,
+                const int32_t *seeds, int32_t n_seed, const float *eps_q, const int32_t *es_q,
+                int32_t *out_ids, float *out_dist, int32_t *stats, void *ws, size_t ws_bytes,
+                onng_stream_t stream);
+
+/* float32 -> bfloat16 (round to nearest even) copy of a vector set, for X_bf16 */
+int onng_to_bf16(const float *X, int64_t count, uint16_t *out, onng_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ONNG_H */

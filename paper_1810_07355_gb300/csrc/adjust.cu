@@ -1,0 +1,620 @@
+// Graph adjustment on the GPU.
+//
+// Static degree adjustment (Algorithm 2, set form):
+//   N_e(y) = first_{e_o}(N_k(y))  united with  { o : y in first_{e_i}(N_k(o)) }.
+// The reversed edge y->o carries the length stored for o->y; it is skipped when
+// y->o is already one of y's forward edges (the forward length wins).  The
+// count pass computes every row's exact size (forward edges plus non-duplicate
+// reversed edges), a device scan turns the sizes into row_ptr, the fill pass
+// writes (length, id) keys, and each row is sorted by (length, id): a warp
+// register bitonic sort for rows up to 512 edges, an in-place CTA sort for
+// longer rows (hubs).
+//
+// Path adjustment (Algorithms 4/5, order-free reading): edge (i, j) is dropped
+// if the input graph holds i->m and m->j with len(i,m) < len(i,j) and
+// len(m,j) < len(i,j).  A warp owns a node i: N(i) goes into a shared-memory
+// hash (id -> position); the adjacency lists of all m in N(i) are streamed as
+// one flattened sequence across the lanes, and every hit j that satisfies both
+// strict comparisons records the smallest witness position.  Nodes with more
+// than 256 edges use a CTA and a hash in global scratch.  A count / scan /
+// compact sequence then writes the kept edges in their input order.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "scan.cuh"
+#include "warp_sort.cuh"
+
+namespace onng {
+namespace {
+
+constexpr unsigned long long EMPTY_KEY = 0x7F800000FFFFFFFFull;
+
+__device__ __forceinline__ bool in_first(const int32_t *__restrict__ nbr, int64_t row, int k, int f, int32_t id)
+{
+    const int32_t *p = nbr + row * k;
+    for (int t = 0; t < f; ++t)
+        if (p[t] == id)
+            return true;
+    return false;
+}
+
+__device__ __forceinline__ int valid_prefix(const int32_t *__restrict__ nbr, int64_t row, int k, int f)
+{
+    int c = 0;
+    for (int t = 0; t < f; ++t)
+        c += nbr[row * k + t] >= 0;
+    return c;
+}
+
+// deg[y] = valid forward edges of y; incnt[y] += non-duplicate reversed edges.
+__global__ void degree_count_kernel(const int32_t *__restrict__ nbr, int64_t n, int k, int fo, int fi,
+                                    int64_t *__restrict__ deg, int *__restrict__ incnt)
+{
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+        for (int p = 0; p < fi; ++p) {
+            const int32_t y = nbr[o * k + p];
+            if (y < 0 || y >= n)
+                continue;
+            if (!in_first(nbr, y, k, fo, (int32_t)o))
+                atomicAdd(&incnt[y], 1);
+        }
+    }
+}
+
+__global__ void degree_total_kernel(const int32_t *__restrict__ nbr, int64_t n, int k, int fo,
+                                    const int *__restrict__ incnt, int64_t *__restrict__ deg)
+{
+    for (int64_t y = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; y < n; y += (int64_t)gridDim.x * blockDim.x)
+        deg[y] = valid_prefix(nbr, y, k, fo) + incnt[y];
+}
+
+__global__ void degree_fill_kernel(const int32_t *__restrict__ nbr, const float *__restrict__ len, int64_t n, int k,
+                                   int fo, int fi, const int64_t *__restrict__ row_ptr, int *__restrict__ cursor,
+                                   unsigned long long *__restrict__ keys)
+{
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+        // forward edges of o occupy the head of its row
+        int w = 0;
+        for (int p = 0; p < fo; ++p) {
+            const int32_t x = nbr[o * k + p];
+            if (x >= 0)
+                keys[row_ptr[o] + w++] = pack_key(len[o * k + p], x);
+        }
+        // reversed edges y->o go after y's forward edges
+        for (int p = 0; p < fi; ++p) {
+            const int32_t y = nbr[o * k + p];
+            if (y < 0 || y >= n)
+                continue;
+            if (in_first(nbr, y, k, fo, (int32_t)o))
+                continue;
+            const int pos = atomicAdd(&cursor[y], 1);
+            keys[row_ptr[y] + valid_prefix(nbr, y, k, fo) + pos] = pack_key(len[o * k + p], (int32_t)o);
+        }
+    }
+}
+
+// Sorts rows of up to 512 keys, one warp per row; longer rows are listed for the CTA sort.
+__global__ void sort_small_rows(const int64_t *__restrict__ row_ptr, int64_t n, unsigned long long *__restrict__ keys,
+                                int64_t *__restrict__ big_rows, int *__restrict__ n_big)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (row >= n)
+        return;
+    const int64_t beg = row_ptr[row], m = row_ptr[row + 1] - beg;
+    if (m <= 1)
+        return;
+    if (m > 512) {
+        if (lane == 0)
+            big_rows[atomicAdd(n_big, 1)] = row;
+        return;
+    }
+    unsigned long long v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int e = i * 32 + lane;
+        v[i] = e < m ? keys[beg + e] : EMPTY_KEY;
+    }
+    warp_bitonic_sort<16>(v, lane);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int e = i * 32 + lane;
+        if (e < m)
+            keys[beg + e] = v[i];
+    }
+}
+
+// In-place ascending sort of a[0..m) by one CTA: bitonic network in the form
+// whose comparators all point upward (first stage of each merge compares
+// mirrored positions), so positions >= m act as +inf and are never touched.
+__device__ void cta_sort(unsigned long long *a, int64_t m)
+{
+    int64_t P = 1;
+    while (P < m)
+        P <<= 1;
+    for (int64_t size = 2; size <= P; size <<= 1) {
+        for (int64_t t = threadIdx.x; t < P / 2; t += blockDim.x) {
+            const int64_t blk = t / (size / 2), off = t % (size / 2);
+            const int64_t i = blk * size + off, j = blk * size + size - 1 - off;
+            if (j < m && a[j] < a[i]) {
+                unsigned long long x = a[i];
+                a[i] = a[j];
+                a[j] = x;
+            }
+        }
+        __syncthreads();
+        for (int64_t h = size / 4; h >= 1; h >>= 1) {
+            for (int64_t t = threadIdx.x; t < P / 2; t += blockDim.x) {
+                const int64_t blk = t / h, off = t % h;
+                const int64_t i = blk * 2 * h + off, j = i + h;
+                if (j < m && a[j] < a[i]) {
+                    unsigned long long x = a[i];
+                    a[i] = a[j];
+                    a[j] = x;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void sort_big_rows(const int64_t *__restrict__ row_ptr, unsigned long long *__restrict__ keys,
+                              const int64_t *__restrict__ big_rows, const int *__restrict__ n_big)
+{
+    for (int b = blockIdx.x; b < *n_big; b += gridDim.x) {
+        const int64_t row = big_rows[b];
+        cta_sort(keys + row_ptr[row], row_ptr[row + 1] - row_ptr[row]);
+        __syncthreads();
+    }
+}
+
+__global__ void unpack_keys(const unsigned long long *__restrict__ keys, const int64_t *__restrict__ nnz,
+                            int32_t *__restrict__ col, float *__restrict__ len)
+{
+    const int64_t m = *nnz;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long k = keys[e];
+        col[e] = (int32_t)(unsigned)(k & 0xFFFFFFFFull);
+        len[e] = __uint_as_float((unsigned)(k >> 32));
+    }
+}
+
+// ------------------------------------------------------------------ path
+
+constexpr int kPathSmall = 256;       // rows up to this many edges: one warp, shared-memory hash
+constexpr int kPathHash = 512;        // hash slots for small rows
+constexpr int kPathWarps = 4;
+
+struct PathSmem {
+    int hkey[kPathHash];
+    int hpos[kPathHash];
+    float li[kPathSmall];
+    int wit[kPathSmall];
+    int64_t pre[32];
+    int64_t mb[32];
+    int mu[32];
+};
+
+__device__ __forceinline__ unsigned phash(int id) { return static_cast<unsigned>(id) * 0x9E3779B1u; }
+
+// Looks id up in an open-addressing table of `cap` slots; returns its position or -1.
+__device__ __forceinline__ int hash_find(const int *hkey, const int *hpos, int cap, int lg, int id)
+{
+    unsigned h = phash(id) >> (32 - lg);
+    for (int t = 0; t < cap; ++t) {
+        const int k = hkey[h];
+        if (k == id)
+            return hpos[h];
+        if (k == -1)
+            return -1;
+        h = (h + 1) & (cap - 1);
+    }
+    return -1;
+}
+
+__device__ __forceinline__ void hash_put(int *hkey, int *hpos, int cap, int lg, int id, int pos)
+{
+    unsigned h = phash(id) >> (32 - lg);
+    for (int t = 0; t < cap; ++t) {
+        const int old = atomicCAS(&hkey[h], -1, id);
+        if (old == -1 || old == id) {
+            hpos[h] = pos;
+            return;
+        }
+        h = (h + 1) & (cap - 1);
+    }
+}
+
+// Marks removals of the edges of node i (deg <= kPathSmall) by one warp.
+__device__ void path_row_warp(int64_t i, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                              const float *__restrict__ len, PathSmem &sm, int *__restrict__ wit_out, int lane)
+{
+    const int64_t beg = rp[i];
+    const int deg = (int)(rp[i + 1] - beg);
+    constexpr int lg = 9;  // log2(kPathHash)
+    for (int t = lane; t < kPathHash; t += 32)
+        sm.hkey[t] = -1;
+    __syncwarp();
+    for (int t = lane; t < deg; t += 32) {
+        const int j = col[beg + t];
+        sm.li[t] = len[beg + t];
+        sm.wit[t] = INT_MAX;
+        hash_put(sm.hkey, sm.hpos, kPathHash, lg, j, t);
+    }
+    __syncwarp();
+    float lmax = 0.f;
+    for (int t = lane; t < deg; t += 32)
+        lmax = fmaxf(lmax, sm.li[t]);
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1)
+        lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, off));
+    for (int u0 = 0; u0 < deg; u0 += 32) {
+        const int u = u0 + lane;
+        int64_t cnt = 0, mb = 0;
+        if (u < deg && sm.li[u] < lmax) {
+            const int m = col[beg + u];
+            mb = rp[m];
+            cnt = rp[m + 1] - mb;
+        }
+        int64_t x = cnt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off)
+                x += y;
+        }
+        sm.pre[lane] = x;  // inclusive prefix
+        sm.mb[lane] = mb;
+        sm.mu[lane] = u;
+        __syncwarp();
+        const int64_t total = sm.pre[31];
+        for (int64_t e = lane; e < total; e += 32) {
+            int lo = 0, hi = 31;  // first lane whose inclusive prefix exceeds e
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (sm.pre[mid] > e)
+                    hi = mid;
+                else
+                    lo = mid + 1;
+            }
+            const int64_t start = sm.pre[lo] - (lo ? sm.pre[lo - 1] : 0);
+            const int64_t off = e - (sm.pre[lo] - start);
+            const int64_t idx = sm.mb[lo] + off;
+            const float lmj = len[idx];
+            if (!(lmj < lmax))
+                continue;
+            const int t = hash_find(sm.hkey, sm.hpos, kPathHash, lg, col[idx]);
+            if (t < 0)
+                continue;
+            const int uu = sm.mu[lo];
+            const float lij = sm.li[t];
+            if (sm.li[uu] < lij && lmj < lij)
+                atomicMin(&sm.wit[t], uu);
+        }
+        __syncwarp();
+    }
+    for (int t = lane; t < deg; t += 32)
+        wit_out[beg + t] = sm.wit[t] == INT_MAX ? -1 : sm.wit[t];
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kPathWarps * 32)
+    path_small_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const float *__restrict__ len,
+                      int64_t n, int *__restrict__ wit, int64_t *__restrict__ big_rows, int *__restrict__ n_big)
+{
+    __shared__ PathSmem sm[kPathWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * kPathWarps + warp;
+    if (i >= n)
+        return;
+    const int64_t deg = rp[i + 1] - rp[i];
+    if (deg > kPathSmall) {
+        if (lane == 0)
+            big_rows[atomicAdd(n_big, 1)] = i;
+        return;
+    }
+    if (deg >= 2)
+        path_row_warp(i, rp, col, len, sm[warp], wit, lane);
+    else if (deg == 1 && lane == 0)
+        wit[rp[i]] = -1;
+}
+
+// Open-addressing table of any size `cap` (range reduction by multiply-high).
+__device__ __forceinline__ int ghash_find(const int *hkey, const int *hpos, int cap, int id)
+{
+    unsigned h = __umulhi(phash(id), (unsigned)cap);
+    for (int t = 0; t < cap; ++t) {
+        const int k = hkey[h];
+        if (k == id)
+            return hpos[h];
+        if (k == -1)
+            return -1;
+        h = h + 1 == (unsigned)cap ? 0 : h + 1;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ void ghash_put(int *hkey, int *hpos, int cap, int id, int pos)
+{
+    unsigned h = __umulhi(phash(id), (unsigned)cap);
+    for (int t = 0; t < cap; ++t) {
+        const int old = atomicCAS(&hkey[h], -1, id);
+        if (old == -1 || old == id) {
+            hpos[h] = pos;
+            return;
+        }
+        h = h + 1 == (unsigned)cap ? 0 : h + 1;
+    }
+}
+
+// Rows with more than kPathSmall edges: one CTA per row; the row's hash lives in
+// global scratch at offset 2 * row_ptr[i] (2 * degree slots, so rows never overlap).
+__global__ void path_big_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                const float *__restrict__ len, int *__restrict__ wit,
+                                const int64_t *__restrict__ big_rows, const int *__restrict__ n_big,
+                                int *__restrict__ skey, int *__restrict__ spos)
+{
+    __shared__ float s_lmax;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int b = blockIdx.x; b < *n_big; b += gridDim.x) {
+        const int64_t i = big_rows[b];
+        const int64_t beg = rp[i];
+        const int deg = (int)(rp[i + 1] - beg);
+        const int cap = 2 * deg;
+        int *hkey = skey + 2 * beg;
+        int *hpos = spos + 2 * beg;
+        for (int t = threadIdx.x; t < cap; t += blockDim.x)
+            hkey[t] = -1;
+        if (threadIdx.x == 0)
+            s_lmax = 0.f;
+        __syncthreads();
+        for (int t = threadIdx.x; t < deg; t += blockDim.x) {
+            wit[beg + t] = INT_MAX;
+            ghash_put(hkey, hpos, cap, col[beg + t], t);
+        }
+        if (threadIdx.x == 0)
+            s_lmax = len[beg + deg - 1];  // rows are sorted by length
+        __syncthreads();
+        const float lmax = s_lmax;
+        for (int u = warp; u < deg; u += nw) {
+            const float liu = len[beg + u];
+            if (!(liu < lmax))
+                continue;
+            const int m = col[beg + u];
+            const int64_t mb = rp[m], me = rp[m + 1];
+            for (int64_t idx = mb + lane; idx < me; idx += 32) {
+                const float lmj = len[idx];
+                if (!(lmj < lmax))
+                    break;
+                const int t = ghash_find(hkey, hpos, cap, col[idx]);
+                if (t < 0)
+                    continue;
+                const float lij = len[beg + t];
+                if (liu < lij && lmj < lij)
+                    atomicMin(&wit[beg + t], u);
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < deg; t += blockDim.x)
+            if (wit[beg + t] == INT_MAX)
+                wit[beg + t] = -1;
+        __syncthreads();
+    }
+}
+
+__global__ void path_count_kernel(const int64_t *__restrict__ rp, int64_t n, const int *__restrict__ wit,
+                                  int64_t *__restrict__ kept)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (i >= n)
+        return;
+    int64_t c = 0;
+    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += 32)
+        c += wit[e] < 0;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1)
+        c += __shfl_xor_sync(0xffffffffu, c, off);
+    if (lane == 0)
+        kept[i] = c;
+}
+
+__global__ void path_compact_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                    const float *__restrict__ len, int64_t n, const int *__restrict__ wit,
+                                    const int64_t *__restrict__ rp_out, int32_t *__restrict__ col_out,
+                                    float *__restrict__ len_out, int32_t *__restrict__ removed_by)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (i >= n)
+        return;
+    const int64_t beg = rp[i], end = rp[i + 1];
+    int64_t w = rp_out[i];
+    for (int64_t e0 = beg; e0 < end; e0 += 32) {
+        const int64_t e = e0 + lane;
+        const bool keep = e < end && wit[e] < 0;
+        const unsigned km = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            const int64_t dst = w + __popc(km & ((1u << lane) - 1u));
+            col_out[dst] = col[e];
+            len_out[dst] = len[e];
+        }
+        if (removed_by && e < end)
+            removed_by[e] = wit[e] < 0 ? -1 : col[beg + wit[e]];
+        w += __popc(km);
+    }
+}
+
+int grid1d(int64_t work, int threads)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>((work + threads - 1) / threads, (int64_t)num_sms() * 16));
+}
+
+}  // namespace
+}  // namespace onng
+
+using namespace onng;
+
+// ------------------------------------------------------------------ degree ABI
+
+extern "C" size_t onng_adjust_degree_workspace_bytes(int64_t n, int32_t k)
+{
+    WsCarver c(nullptr);
+    c.take<int>((size_t)std::max<int64_t>(n, 1));  // in-counts / cursors
+    c.take<int64_t>((size_t)std::max<int64_t>(n, 1));  // row sizes
+    c.take<int64_t>((size_t)std::max<int64_t>(n, 1));  // long rows
+    c.take<int>(64);
+    c.take<char>(scan_workspace_bytes(std::max<int64_t>(n, 1)));
+    c.take<unsigned long long>((size_t)std::max<int64_t>(n, 1) * (size_t)std::max(k, 1) * 2);  // keys
+    return c.used;
+}
+
+static int degree_args(const int32_t *nbr, const float *len, int64_t n, int32_t k, int32_t e_o, int32_t e_i,
+                       void *ws, size_t ws_bytes, const char *who)
+{
+    ONNG_REQUIRE(n >= 0 && n <= INT32_MAX && k >= 1 && e_o >= 0 && e_i >= 0, ONNG_E_INVAL, "%s: bad sizes", who);
+    ONNG_REQUIRE(n == 0 || (nbr && len), ONNG_E_INVAL, "%s: NULL input", who);
+    const size_t need = onng_adjust_degree_workspace_bytes(n, k);
+    ONNG_REQUIRE(ws && ws_bytes >= need, ONNG_E_WORKSPACE, "%s: workspace %zu < %zu bytes", who, ws_bytes, need);
+    return ONNG_OK;
+}
+
+extern "C" int onng_adjust_degree_count(const int32_t *nbr, const float *len, int64_t n, int32_t k, int32_t e_o,
+                                        int32_t e_i, int64_t *row_ptr, int64_t *nnz_host, void *ws, size_t ws_bytes,
+                                        onng_stream_t stream)
+{
+    int st = degree_args(nbr, len, n, k, e_o, e_i, ws, ws_bytes, "onng_adjust_degree_count");
+    if (st)
+        return st;
+    ONNG_REQUIRE(row_ptr, ONNG_E_INVAL, "onng_adjust_degree_count: NULL row_ptr");
+    cudaStream_t s = to_cuda(stream);
+    const int fo = std::min(e_o, k), fi = std::min(e_i, k);
+    WsCarver c(ws);
+    int *incnt = c.take<int>((size_t)std::max<int64_t>(n, 1));
+    int64_t *deg = c.take<int64_t>((size_t)std::max<int64_t>(n, 1));
+    c.take<int64_t>((size_t)std::max<int64_t>(n, 1));
+    c.take<int>(64);
+    char *scan_ws = c.take<char>(scan_workspace_bytes(std::max<int64_t>(n, 1)));
+    if (n > 0) {
+        ONNG_CUDA_TRY(cudaMemsetAsync(incnt, 0, sizeof(int) * n, s), "adjust_degree: clear");
+        degree_count_kernel<<<grid1d(n, 256), 256, 0, s>>>(nbr, n, k, fo, fi, deg, incnt);
+        degree_total_kernel<<<grid1d(n, 256), 256, 0, s>>>(nbr, n, k, fo, incnt, deg);
+        st = check_launch("onng_adjust_degree_count");
+        if (st)
+            return st;
+    }
+    st = exclusive_scan(deg, row_ptr, n, scan_ws, scan_workspace_bytes(std::max<int64_t>(n, 1)), s);
+    if (st)
+        return st;
+    if (nnz_host) {
+        ONNG_CUDA_TRY(cudaMemcpyAsync(nnz_host, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s),
+                      "adjust_degree: nnz");
+        ONNG_CUDA_TRY(cudaStreamSynchronize(s), "adjust_degree: sync");
+    }
+    return ONNG_OK;
+}
+
+extern "C" int onng_adjust_degree(const int32_t *nbr, const float *len, int64_t n, int32_t k, int32_t e_o, int32_t e_i,
+                                  const int64_t *row_ptr, int32_t *col, float *len_out, void *ws, size_t ws_bytes,
+                                  onng_stream_t stream)
+{
+    int st = degree_args(nbr, len, n, k, e_o, e_i, ws, ws_bytes, "onng_adjust_degree");
+    if (st)
+        return st;
+    if (n == 0)
+        return ONNG_OK;
+    ONNG_REQUIRE(row_ptr && col && len_out, ONNG_E_INVAL, "onng_adjust_degree: NULL output");
+    cudaStream_t s = to_cuda(stream);
+    const int fo = std::min(e_o, k), fi = std::min(e_i, k);
+    WsCarver c(ws);
+    int *cursor = c.take<int>((size_t)n);
+    c.take<int64_t>((size_t)n);
+    int64_t *big = c.take<int64_t>((size_t)n);
+    int *n_big = c.take<int>(64);
+    c.take<char>(scan_workspace_bytes(n));
+    unsigned long long *keys = c.take<unsigned long long>((size_t)n * k * 2);
+    ONNG_CUDA_TRY(cudaMemsetAsync(cursor, 0, sizeof(int) * n, s), "adjust_degree: clear");
+    ONNG_CUDA_TRY(cudaMemsetAsync(n_big, 0, sizeof(int), s), "adjust_degree: clear");
+    degree_fill_kernel<<<grid1d(n, 256), 256, 0, s>>>(nbr, len, n, k, fo, fi, row_ptr, cursor, keys);
+    sort_small_rows<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(row_ptr, n, keys, big, n_big);
+    sort_big_rows<<<num_sms() * 2, 1024, 0, s>>>(row_ptr, keys, big, n_big);
+    st = check_launch("onng_adjust_degree: fill/sort");
+    if (st)
+        return st;
+    // the edge count row_ptr[n] is read on the device: no host round trip
+    unpack_keys<<<grid1d(n * (int64_t)(fo + fi), 256), 256, 0, s>>>(keys, row_ptr + n, col, len_out);
+    return check_launch("onng_adjust_degree: unpack");
+}
+
+// ------------------------------------------------------------------ path ABI
+
+extern "C" size_t onng_adjust_path_workspace_bytes(int64_t n, int64_t nnz)
+{
+    WsCarver c(nullptr);
+    c.take<int>((size_t)std::max<int64_t>(nnz, 1));        // witness positions
+    c.take<int>((size_t)std::max<int64_t>(nnz, 1) * 2);    // hub hash keys
+    c.take<int>((size_t)std::max<int64_t>(nnz, 1) * 2);    // hub hash positions
+    c.take<int64_t>((size_t)std::max<int64_t>(n, 1));      // kept counts / long rows
+    c.take<int64_t>((size_t)std::max<int64_t>(n, 1));
+    c.take<int>(64);
+    c.take<unsigned long long>(4);
+    c.take<char>(scan_workspace_bytes(std::max<int64_t>(n, 1)));
+    return c.used;
+}
+
+extern "C" int onng_adjust_path(const int64_t *row_ptr, const int32_t *col, const float *len, int64_t n,
+                                int64_t *row_ptr_out, int32_t *col_out, float *len_out, int64_t *nnz_host,
+                                int32_t *removed_by, void *ws, size_t ws_bytes, onng_stream_t stream)
+{
+    ONNG_REQUIRE(n >= 0 && n <= INT32_MAX, ONNG_E_INVAL, "onng_adjust_path: bad n");
+    ONNG_REQUIRE(row_ptr && row_ptr_out, ONNG_E_INVAL, "onng_adjust_path: NULL row_ptr");
+    cudaStream_t s = to_cuda(stream);
+    int64_t nnz = 0;
+    ONNG_CUDA_TRY(cudaMemcpyAsync(&nnz, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "adjust_path: nnz");
+    ONNG_CUDA_TRY(cudaStreamSynchronize(s), "adjust_path: sync");
+    const size_t need = onng_adjust_path_workspace_bytes(n, nnz);
+    ONNG_REQUIRE(ws && ws_bytes >= need, ONNG_E_WORKSPACE, "onng_adjust_path: workspace %zu < %zu bytes", ws_bytes,
+                 need);
+    ONNG_REQUIRE(nnz == 0 || (col && len && col_out && len_out), ONNG_E_INVAL, "onng_adjust_path: NULL arrays");
+    WsCarver c(ws);
+    int *wit = c.take<int>((size_t)std::max<int64_t>(nnz, 1));
+    int *skey = c.take<int>((size_t)std::max<int64_t>(nnz, 1) * 2);
+    int *spos = c.take<int>((size_t)std::max<int64_t>(nnz, 1) * 2);
+    int64_t *kept = c.take<int64_t>((size_t)std::max<int64_t>(n, 1));
+    int64_t *big = c.take<int64_t>((size_t)std::max<int64_t>(n, 1));
+    int *n_big = c.take<int>(64);
+    c.take<unsigned long long>(4);
+    char *scan_ws = c.take<char>(scan_workspace_bytes(std::max<int64_t>(n, 1)));
+    int st;
+    if (n > 0) {
+        ONNG_CUDA_TRY(cudaMemsetAsync(n_big, 0, sizeof(int), s), "adjust_path: clear");
+        path_small_kernel<<<(unsigned)((n + kPathWarps - 1) / kPathWarps), kPathWarps * 32, 0, s>>>(
+            row_ptr, col, len, n, wit, big, n_big);
+        // hub rows: the kernel reads the count of listed rows on the device
+        path_big_kernel<<<num_sms() * 2, 512, 0, s>>>(row_ptr, col, len, wit, big, n_big, skey, spos);
+        st = check_launch("onng_adjust_path: mark");
+        if (st)
+            return st;
+        path_count_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(row_ptr, n, wit, kept);
+        st = check_launch("onng_adjust_path: count");
+        if (st)
+            return st;
+    }
+    st = exclusive_scan(kept, row_ptr_out, n, scan_ws, scan_workspace_bytes(std::max<int64_t>(n, 1)), s);
+    if (st)
+        return st;
+    if (n > 0) {
+        path_compact_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(row_ptr, col, len, n, wit, row_ptr_out,
+                                                                           col_out, len_out, removed_by);
+        st = check_launch("onng_adjust_path: compact");
+        if (st)
+            return st;
+    }
+    if (nnz_host) {
+        ONNG_CUDA_TRY(cudaMemcpyAsync(nnz_host, row_ptr_out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s),
+                      "adjust_path: nnz");
+        ONNG_CUDA_TRY(cudaStreamSynchronize(s), "adjust_path: sync");
+    }
+    return ONNG_OK;
+}

@@ -1,0 +1,298 @@
+"""Python binding of the onng C ABI (``include/onng.h``).
+
+Argument marshalling only: every step runs in ``libonng.so``'s CUDA kernels.
+Tensors are torch CUDA tensors; the current torch stream is passed to every call.
+If the library cannot be loaded the calls raise: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+ONNG_OK, ONNG_E_INVAL, ONNG_E_WORKSPACE, ONNG_E_CUDA, ONNG_E_LIMIT, ONNG_E_UNSUPPORTED = range(6)
+FLAG_S_OVERFLOW, FLAG_VISIT_OVERFLOW, FLAG_LIMIT = 1, 2, 4
+PREC_FP32, PREC_BF16 = 0, 1
+
+
+class OnngError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"onng status {status}: {msg}")
+        self.status = status
+
+
+class _Index(C.Structure):
+    _fields_ = [("row_ptr", C.c_void_p), ("col", C.c_void_p), ("X", C.c_void_p), ("X_bf16", C.c_void_p),
+                ("n", C.c_int64), ("d", C.c_int32), ("pad_", C.c_int32)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("k", C.c_int32), ("e_s", C.c_int32), ("eps", C.c_float), ("precision", C.c_int32),
+                ("k_rerank", C.c_int32), ("max_expansions", C.c_int32)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads (building first if needed) ``libonng.so`` and declares its signatures."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"onng CUDA library not found at {_build.LIB}")
+        lib = C.CDLL(_build.LIB)
+        i32, i64, u64, sz, vp, f32 = C.c_int32, C.c_int64, C.c_uint64, C.c_size_t, C.c_void_p, C.c_float
+        sig = {
+            "onng_last_error": ([], C.c_char_p),
+            "onng_version": ([], C.c_int),
+            "onng_knn_workspace_bytes": ([i64, i32, i64, i32], sz),
+            "onng_knn": ([vp, i64, i32, vp, i64, i32, i64, vp, vp, vp, sz, vp], C.c_int),
+            "onng_build_knng": ([vp, i64, i32, i32, vp, vp, vp, sz, vp], C.c_int),
+            "onng_adjust_degree_workspace_bytes": ([i64, i32], sz),
+            "onng_adjust_degree_count": ([vp, vp, i64, i32, i32, i32, vp, vp, vp, sz, vp], C.c_int),
+            "onng_adjust_degree": ([vp, vp, i64, i32, i32, i32, vp, vp, vp, vp, sz, vp], C.c_int),
+            "onng_adjust_path_workspace_bytes": ([i64, i64], sz),
+            "onng_adjust_path": ([vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, sz, vp], C.c_int),
+            "onng_seeds_random": ([u64, i64, i64, i32, vp, vp], C.c_int),
+            "onng_seeds_pivot_workspace_bytes": ([i64, i32, i32], sz),
+            "onng_seeds_pivot": ([vp, i64, i32, vp, i64, i32, i32, vp, vp, sz, vp], C.c_int),
+            "onng_search_workspace_bytes": ([i64, C.POINTER(_Index), C.POINTER(_Params)], sz),
+            "onng_search": ([C.POINTER(_Index), vp, i64, C.POINTER(_Params), vp, i32, vp, vp, vp, vp, vp, vp, sz, vp],
+                            C.c_int),
+            "onng_to_bf16": ([vp, i64, vp, vp], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def exported_symbols():
+    """Names of the entry points declared in the header."""
+    return [
+        "onng_last_error", "onng_version", "onng_knn_workspace_bytes", "onng_knn", "onng_build_knng",
+        "onng_adjust_degree_workspace_bytes", "onng_adjust_degree_count", "onng_adjust_degree",
+        "onng_adjust_path_workspace_bytes", "onng_adjust_path", "onng_seeds_random",
+        "onng_seeds_pivot_workspace_bytes", "onng_seeds_pivot", "onng_search_workspace_bytes", "onng_search",
+        "onng_to_bf16",
+    ]
+
+
+def _check(status: int):
+    if status != ONNG_OK:
+        raise OnngError(status, load().onng_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ws(nbytes: int, device):
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def _dev(t: torch.Tensor, dtype) -> torch.Tensor:
+    if not t.is_cuda:
+        raise ValueError("onng expects CUDA tensors")
+    return t.to(dtype).contiguous()
+
+
+# ----------------------------------------------------------------------------- kNN graph
+
+def knn(X: torch.Tensor, Q: torch.Tensor, k: int, self_offset: int = -1):
+    """Exact k nearest rows of X for every row of Q: (ids int32 [nq,k], lengths float32 [nq,k])."""
+    X = _dev(X, torch.float32)
+    Q = _dev(Q, torch.float32)
+    n, d = X.shape
+    nq = Q.shape[0]
+    lib = load()
+    nbr = torch.empty((nq, k), dtype=torch.int32, device=X.device)
+    ln = torch.empty((nq, k), dtype=torch.float32, device=X.device)
+    ws = _ws(lib.onng_knn_workspace_bytes(n, d, nq, k), X.device)
+    _check(lib.onng_knn(_ptr(X), n, d, _ptr(Q), nq, k, self_offset, _ptr(nbr), _ptr(ln), _ptr(ws), ws.numel(),
+                        _stream()))
+    return nbr, ln
+
+
+def build_knng(X: torch.Tensor, k: int):
+    """Exact kNN graph of X (self excluded): (nbr int32 [n,k], len float32 [n,k])."""
+    X = _dev(X, torch.float32)
+    n, d = X.shape
+    lib = load()
+    nbr = torch.empty((n, k), dtype=torch.int32, device=X.device)
+    ln = torch.empty((n, k), dtype=torch.float32, device=X.device)
+    ws = _ws(lib.onng_knn_workspace_bytes(n, d, n, k), X.device)
+    _check(lib.onng_build_knng(_ptr(X), n, d, k, _ptr(nbr), _ptr(ln), _ptr(ws), ws.numel(), _stream()))
+    return nbr, ln
+
+
+# ----------------------------------------------------------------------------- adjustment
+
+def adjust_degree(nbr: torch.Tensor, length: torch.Tensor, e_o: int, e_i: int):
+    """Algorithm 2 (set form) on the GPU: CSR (row_ptr int64, col int32, len float32)."""
+    nbr = _dev(nbr, torch.int32)
+    length = _dev(length, torch.float32)
+    n, k = nbr.shape
+    lib = load()
+    dev = nbr.device
+    ws = _ws(lib.onng_adjust_degree_workspace_bytes(n, k), dev)
+    row_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    nnz = C.c_int64(0)
+    _check(lib.onng_adjust_degree_count(_ptr(nbr), _ptr(length), n, k, e_o, e_i, _ptr(row_ptr), C.byref(nnz),
+                                        _ptr(ws), ws.numel(), _stream()))
+    col = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=dev)
+    ln = torch.empty(max(nnz.value, 1), dtype=torch.float32, device=dev)
+    _check(lib.onng_adjust_degree(_ptr(nbr), _ptr(length), n, k, e_o, e_i, _ptr(row_ptr), _ptr(col), _ptr(ln),
+                                  _ptr(ws), ws.numel(), _stream()))
+    return row_ptr, col[:nnz.value], ln[:nnz.value]
+
+
+def adjust_path(row_ptr: torch.Tensor, col: torch.Tensor, length: torch.Tensor, witnesses: bool = False):
+    """Order-free path adjustment on the GPU: CSR (+ witness node per input edge, -1 if kept)."""
+    row_ptr = _dev(row_ptr, torch.int64)
+    col = _dev(col, torch.int32)
+    length = _dev(length, torch.float32)
+    n = row_ptr.numel() - 1
+    m = col.numel()
+    lib = load()
+    dev = row_ptr.device
+    ws = _ws(lib.onng_adjust_path_workspace_bytes(n, m), dev)
+    rp = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    oc = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+    ol = torch.empty(max(m, 1), dtype=torch.float32, device=dev)
+    wit = torch.empty(max(m, 1), dtype=torch.int32, device=dev) if witnesses else None
+    nnz = C.c_int64(0)
+    _check(lib.onng_adjust_path(_ptr(row_ptr), _ptr(col), _ptr(length), n, _ptr(rp), _ptr(oc), _ptr(ol),
+                                C.byref(nnz), _ptr(wit), _ptr(ws), ws.numel(), _stream()))
+    out = (rp, oc[:nnz.value], ol[:nnz.value])
+    return out + (wit[:m],) if witnesses else out
+
+
+# ----------------------------------------------------------------------------- seeds
+
+def seeds_random(global_seed: int, nq: int, n: int, n_seed: int, device="cuda"):
+    out = torch.empty((nq, n_seed), dtype=torch.int32, device=device)
+    _check(load().onng_seeds_random(global_seed, nq, n, n_seed, _ptr(out), _stream()))
+    return out
+
+
+def seeds_pivot(X: torch.Tensor, Q: torch.Tensor, n_pivot: int, n_seed: int):
+    X = _dev(X, torch.float32)
+    Q = _dev(Q, torch.float32)
+    out = torch.empty((Q.shape[0], n_seed), dtype=torch.int32, device=X.device)
+    lib = load()
+    ws = _ws(lib.onng_seeds_pivot_workspace_bytes(X.shape[0], X.shape[1], n_pivot), X.device)
+    _check(lib.onng_seeds_pivot(_ptr(X), X.shape[0], X.shape[1], _ptr(Q), Q.shape[0], n_pivot, n_seed, _ptr(out),
+                                _ptr(ws), ws.numel(), _stream()))
+    return out
+
+
+def to_bf16(X: torch.Tensor) -> torch.Tensor:
+    """bfloat16 (round to nearest even) copy made by the library's kernel."""
+    X = _dev(X, torch.float32)
+    out = torch.empty(X.shape, dtype=torch.bfloat16, device=X.device)
+    _check(load().onng_to_bf16(_ptr(X), X.numel(), _ptr(out), _stream()))
+    return out
+
+
+# ----------------------------------------------------------------------------- search
+
+@dataclass
+class Index:
+    """A device-resident index: adjusted graph (CSR) and vectors."""
+    row_ptr: torch.Tensor
+    col: torch.Tensor
+    X: torch.Tensor
+    X_bf16: torch.Tensor | None = None
+    length: torch.Tensor | None = None
+
+    @property
+    def n(self) -> int:
+        return self.X.shape[0]
+
+    @property
+    def d(self) -> int:
+        return self.X.shape[1]
+
+    def with_bf16(self) -> "Index":
+        if self.X_bf16 is None:
+            self.X_bf16 = to_bf16(self.X)
+        return self
+
+    def _c(self) -> _Index:
+        return _Index(self.row_ptr.data_ptr(), self.col.data_ptr(), self.X.data_ptr(),
+                      0 if self.X_bf16 is None else self.X_bf16.data_ptr(), self.n, self.d, 0)
+
+
+def build_index(X: torch.Tensor, k: int, e_o: int, e_i: int, path: bool = True) -> Index:
+    """Algorithm ConstructGraph with the exact kNN graph: kNNG -> degree -> path adjustment."""
+    X = _dev(X, torch.float32)
+    nbr, ln = build_knng(X, k)
+    g = adjust_degree(nbr, ln, e_o, e_i)
+    if path:
+        g = adjust_path(*g)
+    return Index(g[0], g[1], X, None, g[2])
+
+
+class SearchWorkspace:
+    """Reusable device workspace for ``search`` (grows on demand)."""
+
+    def __init__(self):
+        self.buf = None
+
+    def get(self, nbytes: int, device):
+        if self.buf is None or self.buf.numel() < nbytes or self.buf.device != torch.device(device):
+            self.buf = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+        return self.buf
+
+
+_default_ws = SearchWorkspace()
+
+
+def search(index: Index, Q: torch.Tensor, k: int, e_s: int, eps: float, seeds: torch.Tensor,
+           precision: int = PREC_FP32, k_rerank: int = 0, eps_q: torch.Tensor | None = None,
+           es_q: torch.Tensor | None = None, max_expansions: int = 0, stats: bool = True,
+           workspace: SearchWorkspace | None = None, out=None):
+    """Algorithm 1 for every query row: (ids int32 [nq,k], dist float32 [nq,k], stats int32 [nq,4] or None)."""
+    Q = _dev(Q, torch.float32)
+    seeds = _dev(seeds, torch.int32)
+    nq = Q.shape[0]
+    dev = Q.device
+    lib = load()
+    if precision == PREC_BF16:
+        index.with_bf16()
+    p = _Params(k, e_s, float(eps) if math.isfinite(eps) else math.inf, precision, k_rerank, max_expansions)
+    ic = index._c()
+    need = lib.onng_search_workspace_bytes(nq, C.byref(ic), C.byref(p))
+    ws = (workspace or _default_ws).get(need, dev)
+    if out is None:
+        ids = torch.empty((nq, k), dtype=torch.int32, device=dev)
+        dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
+        st = torch.empty((nq, 4), dtype=torch.int32, device=dev) if stats else None
+    else:
+        ids, dist, st = out
+    eq = None if eps_q is None else _dev(eps_q, torch.float32)
+    sq = None if es_q is None else _dev(es_q, torch.int32)
+    _check(lib.onng_search(C.byref(ic), _ptr(Q), nq, C.byref(p), _ptr(seeds), seeds.shape[1], _ptr(eq), _ptr(sq),
+                           _ptr(ids), _ptr(dist), _ptr(st), _ptr(ws), ws.numel(), _stream()))
+    return ids, dist, st

@@ -1,0 +1,66 @@
+"""The C-ABI library builds, loads and exports every entry point the header declares.
+
+These run without a GPU: only symbol lookup and argument checks that return
+before any CUDA call.
+"""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(onng_\w+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1810_07355_gb300 import onng
+    return onng.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared()
+    assert len(declared) >= 16
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_header():
+    from paper_1810_07355_gb300 import onng
+    assert set(onng.exported_symbols()) <= _declared()
+
+
+def test_version_and_argument_checks(lib):
+    from paper_1810_07355_gb300 import onng
+    assert lib.onng_version() >= 1
+    # rejected before any CUDA call: bad sizes, unsupported d / k
+    st = lib.onng_knn(None, 10, 6, None, 10, 5, -1, None, None, None, 0, None)
+    assert st == onng.ONNG_E_UNSUPPORTED and b"multiple of 4" in lib.onng_last_error()
+    st = lib.onng_knn(None, 10, 8, None, 10, 500, -1, None, None, None, 0, None)
+    assert st == onng.ONNG_E_UNSUPPORTED
+    st = lib.onng_knn(None, -1, 8, None, 10, 5, -1, None, None, None, 0, None)
+    assert st == onng.ONNG_E_INVAL
+    st = lib.onng_seeds_random(1, 4, 100, 0, None, None)
+    assert st == onng.ONNG_E_UNSUPPORTED
+    st = lib.onng_seeds_random(1, 4, 0, 4, None, None)
+    assert st == onng.ONNG_E_INVAL
+    p = onng._Params(0, 10, 0.1, 0, 0, 0)
+    ix = onng._Index(None, None, None, None, 100, 128, 0)
+    st = lib.onng_search(C.byref(ix), None, 5, C.byref(p), None, 4, None, None, None, None, None, None, 0, None)
+    assert st == onng.ONNG_E_UNSUPPORTED and b"k must be" in lib.onng_last_error()
+    ix = onng._Index(None, None, None, None, 100, 130, 0)
+    p = onng._Params(10, 10, 0.1, 0, 0, 0)
+    st = lib.onng_search(C.byref(ix), None, 5, C.byref(p), None, 4, None, None, None, None, None, None, 0, None)
+    assert st == onng.ONNG_E_UNSUPPORTED
+    st = lib.onng_adjust_degree_count(None, None, -5, 10, 3, 3, None, None, None, 0, None)
+    assert st == onng.ONNG_E_INVAL

@@ -1,0 +1,299 @@
+"""GPU parity: every CUDA step against the CPU FP64 oracle on the same inputs.
+
+Integer-valued inputs (the image-descriptor workload) are ranked exactly in
+float32, so graphs, seeds and search results must match the oracle bit for bit.
+Float inputs may differ only where two competing distances are within 1e-5
+relative.  Each step is fed the same input on both sides (stepwise parity).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1810_07355_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def onng():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1810_07355_gb300 import onng as m
+    m.load()
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def assert_rows_match(ids, lens, o_ids, o_lens, exact=True):
+    """Rows equal; without `exact`, swaps are allowed only among near-equal distances."""
+    if exact:
+        assert np.array_equal(ids, o_ids)
+        np.testing.assert_allclose(lens, o_lens, rtol=1e-6)
+        return
+    bad = np.nonzero((ids != o_ids).any(1))[0]
+    for r in bad:
+        # the multiset of distances must agree, and every id mismatch sits at a near-tie
+        np.testing.assert_allclose(np.sort(lens[r]), np.sort(o_lens[r]), rtol=REL)
+        for c in np.nonzero(ids[r] != o_ids[r])[0]:
+            near = np.abs(o_lens[r] - o_lens[r, c]) <= REL * o_lens[r, c]
+            assert near.sum() >= 2 or c == ids.shape[1] - 1, (r, c)
+    assert len(bad) <= max(2, 0.01 * len(ids))
+
+
+# ----------------------------------------------------------------------------- kNN graph
+
+@pytest.mark.parametrize("n,k", [(3000, 10), (1037, 40), (2500, 100), (700, 200)])
+def test_knng_integer_exact(onng, n, k):
+    X, _ = synth.workload("sift1m", n=n, nq=1)
+    nbr, ln = onng.build_knng(dev(X), k)
+    o_ids, o_len = oracle.knng(X, k)
+    assert_rows_match(host(nbr), host(ln), o_ids, o_len)
+
+
+def test_knng_tie_heavy_and_duplicates(onng):
+    X = synth.small_integers(1500, 8, high=3, seed=4)  # many duplicate points and equal distances
+    nbr, ln = onng.build_knng(dev(X), 24)
+    o_ids, o_len = oracle.knng(X, 24)
+    assert_rows_match(host(nbr), host(ln), o_ids, o_len)
+
+
+def test_knng_float_near_ties_only(onng):
+    X, _ = synth.workload("gmm10k", n=2000, nq=1)
+    nbr, ln = onng.build_knng(dev(X), 40)
+    o_ids, o_len = oracle.knng(X, 40)
+    assert_rows_match(host(nbr), host(ln), o_ids, o_len, exact=False)
+
+
+def test_knn_queries_ground_truth(onng):
+    X, Q = synth.workload("sift1m", n=4000, nq=300)
+    ids, ln = onng.knn(dev(X), dev(Q), 10)
+    o_ids, o_len = oracle.knn(X, Q, 10)
+    assert_rows_match(host(ids), host(ln), o_ids, o_len)
+
+
+def test_knn_padding_small_base(onng):
+    X = synth.small_integers(20, 4, high=50, seed=2)
+    ids, ln = onng.build_knng(dev(X), 19)
+    o_ids, o_len = oracle.knng(X, 19)
+    assert_rows_match(host(ids), host(ln), o_ids, o_len)
+
+
+# ----------------------------------------------------------------------------- adjustment
+
+def _csr_equal(g, o):
+    ptr, col, ln = (host(t) for t in g)
+    assert np.array_equal(ptr, o[0])
+    assert np.array_equal(col, o[1])
+    np.testing.assert_array_equal(ln.astype(np.float64), o[2])
+
+
+@pytest.fixture(scope="module")
+def sift_knng(onng):
+    X, Q = synth.workload("sift1m", n=6000, nq=200)
+    nbr, ln = onng.build_knng(dev(X), 40)
+    return X, Q, nbr, ln
+
+
+@pytest.mark.parametrize("e_o,e_i", [(10, 30), (40, 0), (0, 40), (20, 20), (5, 13)])
+def test_degree_stepwise(onng, sift_knng, e_o, e_i):
+    _, _, nbr, ln = sift_knng
+    g = onng.adjust_degree(nbr, ln, e_o, e_i)
+    o = oracle.adjust_degree(host(nbr), host(ln).astype(np.float64), e_o, e_i)
+    _csr_equal(g, o)
+
+
+def _hub_knng(onng, n=3000):
+    # a dense cluster with a few central points that sit in almost every list
+    rng = np.random.default_rng(5)
+    X = np.rint(rng.normal(100, 20, size=(n, 16))).clip(0, 255).astype(np.float32)
+    X[:3] = 100.0
+    nbr, ln = onng.build_knng(dev(X), 40)
+    return X, nbr, ln
+
+
+def test_degree_hub_rows(onng):
+    _, nbr, ln = _hub_knng(onng)
+    g = onng.adjust_degree(nbr, ln, 10, 40)
+    deg = np.diff(host(g[0]))
+    assert deg.max() > 512  # exercises the CTA sort
+    o = oracle.adjust_degree(host(nbr), host(ln).astype(np.float64), 10, 40)
+    _csr_equal(g, o)
+
+
+@pytest.mark.parametrize("e_o,e_i", [(10, 30), (20, 20)])
+def test_path_stepwise(onng, sift_knng, e_o, e_i):
+    _, _, nbr, ln = sift_knng
+    g = onng.adjust_degree(nbr, ln, e_o, e_i)
+    p = onng.adjust_path(*g, witnesses=True)
+    o = oracle.adjust_path(host(g[0]), host(g[1]), host(g[2]).astype(np.float64), witnesses=True)
+    _csr_equal(p[:3], o[:3])
+    assert np.array_equal(host(p[3]), o[3])
+
+
+def test_path_hub_rows(onng):
+    _, nbr, ln = _hub_knng(onng)
+    g = onng.adjust_degree(nbr, ln, 10, 40)
+    assert np.diff(host(g[0])).max() > 256  # exercises the CTA kernel
+    p = onng.adjust_path(*g, witnesses=True)
+    o = oracle.adjust_path(host(g[0]), host(g[1]), host(g[2]).astype(np.float64), witnesses=True)
+    _csr_equal(p[:3], o[:3])
+    assert np.array_equal(host(p[3]), o[3])
+
+
+def test_path_float_lengths(onng):
+    X, _ = synth.workload("gmm10k", n=3000, nq=1)
+    nbr, ln = onng.build_knng(dev(X), 30)
+    g = onng.adjust_degree(nbr, ln, 10, 20)
+    p = onng.adjust_path(*g)
+    o = oracle.adjust_path(host(g[0]), host(g[1]), host(g[2]).astype(np.float64))
+    _csr_equal(p, o)
+
+
+# ----------------------------------------------------------------------------- seeds
+
+def test_seeds_random_bit_exact(onng):
+    for n, ns in [(1000, 10), (10**6, 64), (7, 3), (5, 5)]:
+        s = onng.seeds_random(77, 500, n, ns)
+        assert np.array_equal(host(s), oracle.seeds_random(77, 500, n, ns))
+
+
+def test_seeds_pivot_integer_exact(onng):
+    X, Q = synth.workload("sift1m", n=20000, nq=300)
+    s = onng.seeds_pivot(dev(X), dev(Q), 1024, 10)
+    assert np.array_equal(host(s), oracle.seeds_pivot(X, Q, 1024, 10))
+    s = onng.seeds_pivot(dev(X[:50]), dev(Q), 1024, 64)  # fewer pivots than seeds: -1 padded
+    assert np.array_equal(host(s), oracle.seeds_pivot(X[:50], Q, 1024, 64))
+
+
+# ----------------------------------------------------------------------------- search
+
+@pytest.fixture(scope="module")
+def sift_graph(onng, sift_knng):
+    X, Q, nbr, ln = sift_knng
+    g = onng.adjust_path(*onng.adjust_degree(nbr, ln, 10, 30))
+    seeds = onng.seeds_pivot(dev(X), dev(Q), 512, 10)
+    return X, Q, g, seeds
+
+
+@pytest.mark.parametrize("k,e_s,eps", [(10, 10, 0.0), (10, 10, 0.1), (10, 0, 0.05), (1, 5, 0.2),
+                                       (100, 20, 0.05), (10, 10, float("inf")), (128, 0, 0.0)])
+def test_search_integer_exact(onng, sift_graph, k, e_s, eps):
+    X, Q, g, seeds = sift_graph
+    idx = onng.Index(g[0], g[1], dev(X))
+    ids, dist, st = onng.search(idx, dev(Q), k, e_s, eps, seeds)
+    o_ids, o_dist, o_st = oracle.search(host(g[0]), host(g[1]), X, Q, k, e_s, np.float32(eps), host(seeds))
+    assert np.array_equal(host(ids), o_ids)
+    np.testing.assert_allclose(host(dist), o_dist, rtol=1e-6)
+    assert np.array_equal(host(st)[:, 0], o_st[:, 0])  # distance computations
+    assert np.array_equal(host(st)[:, 1], o_st[:, 1])  # expansions
+    assert (host(st)[:, 3] == 0).all()
+
+
+def test_search_unbounded_is_exact_knn(onng, sift_graph):
+    X, Q, g, seeds = sift_graph
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+    n = len(X)
+    A = sp.csr_matrix((np.ones(len(host(g[1]))), host(g[1]), host(g[0])), shape=(n, n))
+    ncomp, lab = connected_components(A, directed=True, connection="strong")
+    ids, dist, st = onng.search(onng.Index(g[0], g[1], dev(X)), dev(Q), 10, 0, float("inf"), seeds)
+    gt, gd = oracle.knn(X, Q, 10)
+    if ncomp == 1:
+        assert np.array_equal(host(ids), gt)
+    assert (host(st)[:, 3] & 2).sum() == 0
+
+
+def test_search_float_data(onng):
+    X, Q = synth.workload("gmm10k", n=4000, nq=150)
+    nbr, ln = onng.build_knng(dev(X), 40)
+    g = onng.adjust_path(*onng.adjust_degree(nbr, ln, 10, 30))
+    seeds = onng.seeds_pivot(dev(X), dev(Q), 1024, 10)
+    ids, dist, st = onng.search(onng.Index(g[0], g[1], dev(X)), dev(Q), 10, 10, 0.05, seeds)
+    o_ids, o_dist, o_st = oracle.search(host(g[0]), host(g[1]), X, Q, 10, 10, np.float32(0.05), host(seeds))
+    same = (host(ids) == o_ids).all(1)
+    assert same.mean() >= 0.98
+    np.testing.assert_allclose(host(dist)[same], o_dist[same], rtol=1e-5)
+
+
+def test_search_edge_cases(onng, sift_graph):
+    X, Q, g, seeds = sift_graph
+    idx = onng.Index(g[0], g[1], dev(X))
+    # no queries
+    ids, dist, st = onng.search(idx, dev(Q[:0]), 10, 10, 0.1, seeds[:0])
+    assert ids.shape == (0, 10)
+    # invalid / repeated seeds are skipped; a query with no valid seed returns padding
+    s = host(seeds).copy()
+    s[0, :] = -1
+    s[1, 1:] = s[1, 0]
+    s[2, 3] = len(X) + 5
+    ids, dist, st = onng.search(idx, dev(Q), 10, 10, 0.1, dev(s))
+    o_ids, o_dist, o_st = oracle.search(host(g[0]), host(g[1]), X, Q, 10, 10, np.float32(0.1),
+                                        np.where(s >= len(X), -1, s))
+    assert (host(ids)[0] == -1).all() and np.isinf(host(dist)[0]).all()
+    assert np.array_equal(host(ids), o_ids)
+    # per-query eps / e_s arrays equal separate calls
+    eq = torch.tensor([0.0, 0.2] * 100, dtype=torch.float32, device="cuda")
+    es = torch.tensor([5, 20] * 100, dtype=torch.int32, device="cuda")
+    ids2, _, st2 = onng.search(idx, dev(Q), 10, 10, 0.1, seeds, eps_q=eq, es_q=es)
+    a, _, _ = onng.search(idx, dev(Q[0::2]), 10, 5, 0.0, seeds[0::2])
+    b, _, _ = onng.search(idx, dev(Q[1::2]), 10, 20, 0.2, seeds[1::2])
+    assert torch.equal(ids2[0::2], a) and torch.equal(ids2[1::2], b)
+    # expansion cap: flagged
+    _, _, st3 = onng.search(idx, dev(Q), 10, 10, 0.2, seeds, max_expansions=3)
+    assert ((host(st3)[:, 3] & onng.FLAG_LIMIT) != 0).any()
+    assert (host(st3)[:, 1] <= 3).all()
+
+
+def test_search_visited_spill(onng):
+    """A query that visits more nodes than the shared-memory table holds spills to
+    the global table and still matches the oracle."""
+    X, Q = synth.workload("sift1m", n=10000, nq=20)
+    nbr, ln = onng.build_knng(dev(X), 40)
+    g = onng.adjust_degree(nbr, ln, 20, 40)
+    seeds = onng.seeds_pivot(dev(X), dev(Q), 256, 10)
+    ids, dist, st = onng.search(onng.Index(g[0], g[1], dev(X)), dev(Q), 100, 0, 0.5, seeds)
+    o_ids, _, o_st = oracle.search(host(g[0]), host(g[1]), X, Q, 100, 0, np.float32(0.5), host(seeds))
+    assert host(st)[:, 2].max() > 3072
+    assert np.array_equal(host(ids), o_ids)
+    assert np.array_equal(host(st)[:, 0], o_st[:, 0])
+
+
+def test_search_bf16_rerank(onng, sift_graph):
+    """Integer data is exact in bfloat16, so the bf16 pass with an FP32 rerank of
+    k_rerank candidates equals the FP32 search with k_rerank results, truncated."""
+    X, Q, g, seeds = sift_graph
+    idx = onng.Index(g[0], g[1], dev(X))
+    ids, dist, st = onng.search(idx, dev(Q), 10, 10, 0.05, seeds, precision=onng.PREC_BF16, k_rerank=20)
+    o_ids, o_dist, o_st = oracle.search(host(g[0]), host(g[1]), X, Q, 20, 10, np.float32(0.05), host(seeds))
+    assert np.array_equal(host(ids), o_ids[:, :10])
+    assert np.array_equal(host(st)[:, 0], o_st[:, 0])
+
+
+def test_search_bf16_float_data(onng):
+    """On float data the bf16 pass follows the oracle run on bf16-rounded vectors;
+    the rerank then uses the exact vectors."""
+    X, Q = synth.workload("gmm10k", n=3000, nq=100)
+    nbr, ln = onng.build_knng(dev(X), 30)
+    g = onng.adjust_path(*onng.adjust_degree(nbr, ln, 10, 20))
+    seeds = onng.seeds_pivot(dev(X), dev(Q), 512, 10)
+    idx = onng.Index(g[0], g[1], dev(X))
+    ids, dist, st = onng.search(idx, dev(Q), 10, 10, 0.05, seeds, precision=onng.PREC_BF16, k_rerank=32)
+    Xb = oracle.bf16_round(X)
+    o_ids, _, _ = oracle.search(host(g[0]), host(g[1]), Xb, Q, 32, 10, np.float32(0.05), host(seeds))
+    # rerank of the oracle's bf16 candidates with exact FP64 distances
+    d64 = np.linalg.norm(X[o_ids].astype(np.float64) - Q[:, None, :].astype(np.float64), axis=2)
+    order = np.lexsort((o_ids, d64), axis=1)[:, :10]
+    want = np.take_along_axis(o_ids, order, 1)
+    same = (host(ids) == want).all(1)
+    assert same.mean() >= 0.95
+    assert torch.equal(onng.to_bf16(dev(X)).float().cpu(), torch.from_numpy(Xb))
