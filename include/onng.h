@@ -129,18 +129,23 @@ int onng_seeds_pivot(const float *X, int64_t n, int32_t d, const float *Q, int64
  * the candidates if d <= r(1+eps) and the results if d <= r; the search ends
  * when the nearest candidate lies beyond r(1+eps).  Seeds are marked visited
  * and counted; R starts as the k nearest seeds with r = +inf until an insertion
- * fills R.  Ties break by (distance, id).  eps = +inf is allowed.
+ * fills R.  Ties break by (distance, id).  eps = +inf is allowed.  The visited
+ * set (Set / IsSet, Sec. 2.5) is exact.
  *
  * The index: row_ptr / col as above (lengths are not needed by the search), X
- * float32 [n, d]; X_bf16 [n, d] (bfloat16 bits, optional) is used when
+ * float32 [n, d].  Optional: adj [n, adj_width] int32, each row's first
+ * adj_width entries padded with -1 (onng_pad_adjacency), used instead of the
+ * CSR lists whenever e_s <= adj_width; X_bf16 [n, d] (bfloat16 bits), used when
  * precision == ONNG_PREC_BF16, in which case the final list of k_rerank >= k
  * candidates is rescored in float32 against X and the best k are returned.
  *
  * Outputs: out_ids [nq, k] int32 and out_dist [nq, k] float32 (Euclidean), sorted
  * by (distance, id), padded -1 / +inf; stats [nq, 4] int32 (optional):
- * distance computations, expansions, visited-set size, ONNG_FLAG_* bits.
+ * distance computations, expansions, adjacency entries scanned, ONNG_FLAG_* bits.
  * eps_q / es_q (optional, [nq]) override eps / e_s per query.
- * Limits: k, k_rerank <= 128, n_seed <= 64, d <= 1024.
+ * Limits: k, k_rerank <= 128, n_seed <= 64, d <= 1024.  The workspace holds
+ * per-warp spill tables (visited ids and candidates beyond the shared-memory
+ * capacity); a smaller workspace than the query runs fewer warps.
  */
 enum onng_precision { ONNG_PREC_FP32 = 0, ONNG_PREC_BF16 = 1 };
 
@@ -149,9 +154,10 @@ typedef struct {
     const int32_t *col;
     const float *X;
     const uint16_t *X_bf16;
+    const int32_t *adj;
     int64_t n;
     int32_t d;
-    int32_t pad_;
+    int32_t adj_width;
 } onng_index;
 
 typedef struct {
@@ -168,6 +174,10 @@ int onng_search(const onng_index *idx, const float *Q, int64_t nq, const onng_se
                 const int32_t *seeds, int32_t n_seed, const float *eps_q, const int32_t *es_q,
                 int32_t *out_ids, float *out_dist, int32_t *stats, void *ws, size_t ws_bytes,
                 onng_stream_t stream);
+
+/* adj [n, width]: the first `width` entries of every CSR row, -1 past its end */
+int onng_pad_adjacency(const int64_t *row_ptr, const int32_t *col, int64_t n, int32_t width,
+                       int32_t *adj, onng_stream_t stream);
 
 /* float32 -> bfloat16 (round to nearest even) copy of a vector set, for X_bf16 */
 int onng_to_bf16(const float *X, int64_t count, uint16_t *out, onng_stream_t stream);

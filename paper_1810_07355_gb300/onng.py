@@ -32,7 +32,7 @@ class OnngError(RuntimeError):
 
 class _Index(C.Structure):
     _fields_ = [("row_ptr", C.c_void_p), ("col", C.c_void_p), ("X", C.c_void_p), ("X_bf16", C.c_void_p),
-                ("n", C.c_int64), ("d", C.c_int32), ("pad_", C.c_int32)]
+                ("adj", C.c_void_p), ("n", C.c_int64), ("d", C.c_int32), ("adj_width", C.c_int32)]
 
 
 class _Params(C.Structure):
@@ -74,6 +74,7 @@ def load(build_if_missing: bool = True):
             "onng_search": ([C.POINTER(_Index), vp, i64, C.POINTER(_Params), vp, i32, vp, vp, vp, vp, vp, vp, sz, vp],
                             C.c_int),
             "onng_to_bf16": ([vp, i64, vp, vp], C.c_int),
+            "onng_pad_adjacency": ([vp, vp, i64, i32, vp, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -90,7 +91,7 @@ def exported_symbols():
         "onng_adjust_degree_workspace_bytes", "onng_adjust_degree_count", "onng_adjust_degree",
         "onng_adjust_path_workspace_bytes", "onng_adjust_path", "onng_seeds_random",
         "onng_seeds_pivot_workspace_bytes", "onng_seeds_pivot", "onng_search_workspace_bytes", "onng_search",
-        "onng_to_bf16",
+        "onng_to_bf16", "onng_pad_adjacency",
     ]
 
 
@@ -207,6 +208,16 @@ def seeds_pivot(X: torch.Tensor, Q: torch.Tensor, n_pivot: int, n_seed: int):
     return out
 
 
+def pad_adjacency(row_ptr: torch.Tensor, col: torch.Tensor, width: int) -> torch.Tensor:
+    """adj [n, width] int32: the first `width` entries of every row, -1 past its end."""
+    row_ptr = _dev(row_ptr, torch.int64)
+    col = _dev(col, torch.int32)
+    n = row_ptr.numel() - 1
+    adj = torch.empty((n, width), dtype=torch.int32, device=row_ptr.device)
+    _check(load().onng_pad_adjacency(_ptr(row_ptr), _ptr(col), n, width, _ptr(adj), _stream()))
+    return adj
+
+
 def to_bf16(X: torch.Tensor) -> torch.Tensor:
     """bfloat16 (round to nearest even) copy made by the library's kernel."""
     X = _dev(X, torch.float32)
@@ -225,6 +236,7 @@ class Index:
     X: torch.Tensor
     X_bf16: torch.Tensor | None = None
     length: torch.Tensor | None = None
+    adj: torch.Tensor | None = None
 
     @property
     def n(self) -> int:
@@ -239,9 +251,17 @@ class Index:
             self.X_bf16 = to_bf16(self.X)
         return self
 
+    def with_adjacency(self, width: int) -> "Index":
+        """Adds the padded first-`width` adjacency table the search reads when e_s <= width."""
+        if self.adj is None or self.adj.shape[1] != width:
+            self.adj = pad_adjacency(self.row_ptr, self.col, width)
+        return self
+
     def _c(self) -> _Index:
         return _Index(self.row_ptr.data_ptr(), self.col.data_ptr(), self.X.data_ptr(),
-                      0 if self.X_bf16 is None else self.X_bf16.data_ptr(), self.n, self.d, 0)
+                      0 if self.X_bf16 is None else self.X_bf16.data_ptr(),
+                      0 if self.adj is None else self.adj.data_ptr(), self.n, self.d,
+                      0 if self.adj is None else self.adj.shape[1])
 
 
 def build_index(X: torch.Tensor, k: int, e_o: int, e_i: int, path: bool = True) -> Index:

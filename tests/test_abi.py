@@ -55,10 +55,10 @@ def test_version_and_argument_checks(lib):
     st = lib.onng_seeds_random(1, 4, 0, 4, None, None)
     assert st == onng.ONNG_E_INVAL
     p = onng._Params(0, 10, 0.1, 0, 0, 0)
-    ix = onng._Index(None, None, None, None, 100, 128, 0)
+    ix = onng._Index(None, None, None, None, None, 100, 128, 0)
     st = lib.onng_search(C.byref(ix), None, 5, C.byref(p), None, 4, None, None, None, None, None, None, 0, None)
     assert st == onng.ONNG_E_UNSUPPORTED and b"k must be" in lib.onng_last_error()
-    ix = onng._Index(None, None, None, None, 100, 130, 0)
+    ix = onng._Index(None, None, None, None, None, 100, 130, 0)
     p = onng._Params(10, 10, 0.1, 0, 0, 0)
     st = lib.onng_search(C.byref(ix), None, 5, C.byref(p), None, 4, None, None, None, None, None, None, 0, None)
     assert st == onng.ONNG_E_UNSUPPORTED

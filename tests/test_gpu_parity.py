@@ -185,11 +185,18 @@ def sift_graph(onng, sift_knng):
     return X, Q, g, seeds
 
 
-@pytest.mark.parametrize("k,e_s,eps", [(10, 10, 0.0), (10, 10, 0.1), (10, 0, 0.05), (1, 5, 0.2),
-                                       (100, 20, 0.05), (10, 10, float("inf")), (128, 0, 0.0)])
-def test_search_integer_exact(onng, sift_graph, k, e_s, eps):
+@pytest.mark.parametrize("k,e_s,eps,padded", [(10, 10, 0.0, False), (10, 10, 0.1, True), (10, 0, 0.05, False),
+                                              (1, 5, 0.2, True), (1, 5, 0.2, False), (10, 10, 0.2, True),
+                                              (10, 5, 0.3, False), (100, 20, 0.05, True),
+                                              (10, 10, float("inf"), False), (128, 0, 0.0, False),
+                                              (10, 40, 0.1, True)])
+def test_search_integer_exact(onng, sift_graph, k, e_s, eps, padded):
+    """Bit-exact against Algorithm 1 in float64, including the searches whose
+    candidate set outgrows the shared-memory pool (eps >= 0.2 spills to global)."""
     X, Q, g, seeds = sift_graph
     idx = onng.Index(g[0], g[1], dev(X))
+    if padded:
+        idx.with_adjacency(max(e_s, 1))
     ids, dist, st = onng.search(idx, dev(Q), k, e_s, eps, seeds)
     o_ids, o_dist, o_st = oracle.search(host(g[0]), host(g[1]), X, Q, k, e_s, np.float32(eps), host(seeds))
     assert np.array_equal(host(ids), o_ids)
@@ -252,6 +259,15 @@ def test_search_edge_cases(onng, sift_graph):
     _, _, st3 = onng.search(idx, dev(Q), 10, 10, 0.2, seeds, max_expansions=3)
     assert ((host(st3)[:, 3] & onng.FLAG_LIMIT) != 0).any()
     assert (host(st3)[:, 1] <= 3).all()
+
+
+def test_pad_adjacency(onng, sift_graph):
+    _, _, g, _ = sift_graph
+    adj = host(onng.pad_adjacency(g[0], g[1], 12))
+    ptr, col = host(g[0]), host(g[1])
+    for i in range(0, len(ptr) - 1, 97):
+        row = col[ptr[i]:ptr[i + 1]][:12]
+        assert np.array_equal(adj[i, :len(row)], row) and (adj[i, len(row):] == -1).all()
 
 
 def test_search_visited_spill(onng):
