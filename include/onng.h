@@ -43,7 +43,7 @@ enum onng_status {
 
 /* per-query flags, stats[q*4 + 3] */
 #define ONNG_FLAG_S_OVERFLOW 1u      /* candidate pool full: farthest candidates dropped */
-#define ONNG_FLAG_VISIT_OVERFLOW 2u  /* visited set full: nodes may be re-evaluated */
+#define ONNG_FLAG_VISIT_OVERFLOW 2u  /* reserved (the visited set cannot overflow) */
 #define ONNG_FLAG_LIMIT 4u           /* max_expansions reached */
 
 const char *onng_last_error(void);
@@ -143,9 +143,10 @@ int onng_seeds_pivot(const float *X, int64_t n, int32_t d, const float *Q, int64
  * by (distance, id), padded -1 / +inf; stats [nq, 4] int32 (optional):
  * distance computations, expansions, adjacency entries scanned, ONNG_FLAG_* bits.
  * eps_q / es_q (optional, [nq]) override eps / e_s per query.
- * Limits: k, k_rerank <= 128, n_seed <= 64, d <= 1024.  The workspace holds
- * per-warp spill tables (visited ids and candidates beyond the shared-memory
- * capacity); a smaller workspace than the query runs fewer warps.
+ * Limits: k, k_rerank <= 128, n_seed <= 64, d <= 1024.  The workspace holds, per
+ * warp, a visited bitmap over the n ids (used past the shared-memory table) and
+ * a spill pool for candidates beyond the register pool; it grows with n, and a
+ * smaller workspace than the query runs fewer warps.
  */
 enum onng_precision { ONNG_PREC_FP32 = 0, ONNG_PREC_BF16 = 1 };
 

@@ -1,19 +1,22 @@
 // KnnSearch (Algorithm 1) on the GPU: one warp per query.
 //
-// Per warp, in shared memory:
-//   - the visited set C as an exact open-addressing hash (linear probing).  The
-//     paper's Set/IsSet table (Sec. 2.5) keeps the first id of a bucket inline and
-//     chains collisions; on the GPU a flat table probed by 32 lanes at once is
-//     cheaper.  Past 3/4 load, new ids go to a per-warp table in global memory.
-//   - the candidate set S as an unsorted pool of (distance, id) keys popped by a
-//     warp-wide min.  An entry beyond r(1+eps) can never be expanded (r only
-//     shrinks, and popping it ends the search), so such entries are dropped
-//     whenever room is needed.  If the in-bound entries still do not fit, the
-//     farther half moves to a per-warp pool in global memory; every key there
-//     is >= tau > every key in shared memory, so the shared pool's minimum is
-//     the minimum of S, and the global pool refills the shared one only when the
-//     latter runs empty.  S stays exact.
-//   - the result set R as a (distance, id)-sorted list of at most k entries.
+// Per warp:
+//   - the visited set C, in shared memory, as an exact open-addressing hash
+//     (linear probing).  The paper's Set/IsSet table (Sec. 2.5) keeps the first
+//     id of a bucket inline and chains collisions; on the GPU a flat table probed
+//     by 32 lanes at once is cheaper.  Past half load, new ids go to a per-warp
+//     bitmap over all n ids in global memory (one atomicOr per id, no probing);
+//     the ids set there are logged and cleared when the query ends.
+//   - the candidate set S in three levels of (distance, id) keys: a sorted head
+//     of up to 32 keys in registers (one per lane: the pop is a shift, an
+//     insertion a ballot plus a shift), an unsorted overflow of up to 256 keys in
+//     shared memory whose keys are all >= every head key, and a per-warp spill
+//     pool in global memory whose keys are all >= tau > every key above it.  So
+//     the head's first key is the minimum of S; a level refills the one above
+//     only when that one runs empty.  An entry beyond r(1+eps) can never be
+//     expanded (r only shrinks, and popping it ends the search), so such entries
+//     are dropped whenever a level is rebuilt.  S stays exact.
+//   - the result set R, in registers, as a sorted list of at most k keys.
 // The up-to-e_s neighbours of the expanded node are tested and their vectors
 // gathered together (coalesced 16-byte loads, several vectors in flight per
 // lane, one transposed butterfly reduction for all of them).  R then takes the k
@@ -21,6 +24,11 @@
 // r(1+eps).  Applying a batch at once yields the same R, the same r after the
 // batch and, since S only loses entries that can never be expanded, the same
 // expansion order as the one-at-a-time loop of Algorithm 1.
+//
+// The node expanded next is known as soon as the batch's distances are: it is
+// the nearer of S's head and the batch's nearest member if that one will be
+// pushed (its distance is within the bound before the batch).  Its adjacency
+// row is loaded right then, so the load overlaps the R and S updates.
 //
 // Adjacency is read from the CSR lists, or from an optional padded table
 // adj [n, width] (-1 padded) that holds each node's first `width` entries, which
@@ -48,12 +56,12 @@ namespace {
 
 typedef unsigned long long u64;
 
+constexpr unsigned FULL = 0xffffffffu;
 constexpr int kWarpsPerCta = 4;
 constexpr int kMaxK = 128;
 constexpr int kMaxSeed = 64;
-constexpr int kPool = 256;           // shared-memory candidate pool entries
-constexpr int kGlobalVisit = 65536;  // per-warp visited spill region (ints): tables of 4K, 8K, 16K, 32K
-constexpr int kSpillFirst = 4096;    // first spill table size; each growth doubles it
+constexpr int kOvf = 256;            // shared-memory overflow keys per warp
+constexpr int kVisitLog = 16384;     // ids logged per warp for clearing its bitmap
 constexpr int kGlobalPool = 16384;   // per-warp candidate spill pool entries
 constexpr u64 kMaxKey = ~0ull;
 
@@ -81,14 +89,15 @@ struct SearchArgs {
     float *out_dist;
     int32_t *stats;
     int *counter;
-    int *gvis;  // [slots, kGlobalVisit]
-    u64 *gpool; // [slots, kGlobalPool]
+    unsigned *gbits;  // [slots, bits_words]: visited bitmap past the shared table
+    int64_t bits_words;
+    int *glog;        // [slots, kVisitLog]: ids set in the bitmap
+    u64 *gpool;       // [slots, kGlobalPool]
 };
 
 template <int HV> struct WarpSmem {
     int vis[HV];
-    u64 pool[kPool];
-    u64 res[kMaxK];
+    u64 ovf[kOvf];
 };
 
 __host__ __device__ constexpr int log2i(int v) { return v <= 1 ? 0 : 1 + log2i(v >> 1); }
@@ -104,11 +113,76 @@ __device__ __forceinline__ u64 warp_min_u64(u64 v)
 {
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) {
-        u64 o = __shfl_xor_sync(0xffffffffu, v, off);
+        u64 o = __shfl_xor_sync(FULL, v, off);
         v = o < v ? o : v;
     }
     return v;
 }
+
+// Ascending list of 32*N keys striped over the warp: element e sits in v[e / 32]
+// of lane e % 32.  Empty slots hold kMaxKey.
+template <int N> struct RegList {
+    u64 v[N];
+
+    __device__ void clear()
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            v[i] = kMaxKey;
+    }
+    // number of elements smaller than key
+    __device__ int rank(u64 key) const
+    {
+        int r = 0;
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            r += __popc(__ballot_sync(FULL, v[i] < key));
+        return r;
+    }
+    // element e (uniform e < 32*N), broadcast to all lanes
+    __device__ u64 get(int e) const
+    {
+        u64 x = kMaxKey;
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if (i == (e >> 5))
+                x = v[i];
+        return __shfl_sync(FULL, x, e & 31);
+    }
+    // inserts key at position pos (uniform); elements at positions >= limit are emptied
+    __device__ void insert_at(int pos, u64 key, int lane, int limit)
+    {
+        u64 carry = kMaxKey;  // old element i*32 - 1
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const u64 up = __shfl_up_sync(FULL, v[i], 1);
+            const u64 last = __shfl_sync(FULL, v[i], 31);
+            const u64 before = lane == 0 ? carry : up;
+            const int e = i * 32 + lane;
+            u64 nv = e < pos ? v[i] : (e == pos ? key : before);
+            v[i] = e < limit ? nv : kMaxKey;
+            carry = last;
+        }
+    }
+    // removes element 0
+    __device__ void pop_front(int lane)
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const u64 down = __shfl_down_sync(FULL, v[i], 1);
+            const u64 next0 = (i + 1 < N) ? __shfl_sync(FULL, v[i + 1], 0) : kMaxKey;
+            v[i] = lane == 31 ? next0 : down;
+        }
+    }
+    // empties every element at position >= m
+    __device__ void truncate(int m, int lane)
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if (i * 32 + lane >= m)
+                v[i] = kMaxKey;
+    }
+};
 
 // Loads 4 consecutive coordinates of a stored vector as float4.
 template <class T> struct Loader;
@@ -145,74 +219,77 @@ __device__ __forceinline__ float sqdiff4(float4 a, float4 b, float acc)
     return fmaf(t, t, acc);
 }
 
-// Sums v[g] over the warp for G values at once.  Afterwards every lane holds
-// the full sum of one value index; holder_lane(g) names a lane holding value g.
+// Sums v[g] over the warp for G values at once (G a power of two <= 16): each
+// butterfly stage halves the values a lane holds by swapping halves with its
+// partner, then plain butterflies finish.  Afterwards every lane holds the full
+// sum of one value index; holder_lane<G>(g) names a lane holding value g.
+template <int G, int OFF> __device__ __forceinline__ void tr_stage(float (&v)[G], int lane, int held)
+{
+    const int half = held >> 1;
+    const bool hi = lane & OFF;
+#pragma unroll
+    for (int i = 0; i < G / 2; ++i) {
+        if (i < half) {
+            float send = hi ? v[i] : v[i + half];
+            float keep = hi ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(FULL, send, OFF);
+        }
+    }
+}
+
 template <int G> __device__ __forceinline__ float transpose_reduce(float (&v)[G], int lane)
 {
-    static_assert(G == 1 || G == 2 || G == 4 || G == 8, "G");
-    if constexpr (G >= 2) {
-        const bool hi = lane & 16;
-#pragma unroll
-        for (int i = 0; i < G / 2; ++i) {
-            float send = hi ? v[i] : v[i + G / 2];
-            float keep = hi ? v[i + G / 2] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-        }
-    }
-    if constexpr (G >= 4) {
-        const bool hi = lane & 8;
-#pragma unroll
-        for (int i = 0; i < G / 4; ++i) {
-            float send = hi ? v[i] : v[i + G / 4];
-            float keep = hi ? v[i + G / 4] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-        }
-    }
-    if constexpr (G >= 8) {
-        const bool hi = lane & 4;
-        float send = hi ? v[0] : v[1];
-        float keep = hi ? v[1] : v[0];
-        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
+    static_assert(G == 1 || G == 2 || G == 4 || G == 8 || G == 16, "G");
+    constexpr int m = log2i(G);
+    if constexpr (m >= 1)
+        tr_stage<G, 16>(v, lane, G);
+    if constexpr (m >= 2)
+        tr_stage<G, 8>(v, lane, G >> 1);
+    if constexpr (m >= 3)
+        tr_stage<G, 4>(v, lane, G >> 2);
+    if constexpr (m >= 4)
+        tr_stage<G, 2>(v, lane, G >> 3);
     float s = v[0];
-    constexpr int first = G == 1 ? 16 : G == 2 ? 8 : G == 4 ? 4 : 2;
 #pragma unroll
-    for (int off = first; off >= 1; off >>= 1)
-        s += __shfl_xor_sync(0xffffffffu, s, off);
+    for (int off = 16 >> m; off >= 1; off >>= 1)
+        s += __shfl_xor_sync(FULL, s, off);
     return s;
 }
 
 template <int G> __device__ __forceinline__ int holder_lane(int g)
 {
-    if constexpr (G == 1)
-        return 0;
-    else if constexpr (G == 2)
-        return g << 4;
-    else if constexpr (G == 4)
-        return ((g >> 1) & 1) << 4 | (g & 1) << 3;
-    else
-        return ((g >> 2) & 1) << 4 | ((g >> 1) & 1) << 3 | (g & 1) << 2;
+    constexpr int m = log2i(G);
+    int l = 0;
+#pragma unroll
+    for (int t = 0; t < m; ++t)
+        l |= ((g >> (m - 1 - t)) & 1) << (4 - t);
+    return l;
 }
 
-template <int V, class T, int HV> struct Warp {
-    static constexpr int G = V >= 8 ? 1 : V >= 4 ? 2 : V >= 2 ? 4 : 8;  // vectors per gather round
+template <int V, class T, int HV, int KR> struct Warp {
+    // vectors per gather round: 16 loads in flight per lane at d <= 128
+    static constexpr int G = V >= 8 ? 2 : V >= 4 ? 4 : V >= 2 ? 8 : 16;
     WarpSmem<HV> &sm;
     const SearchArgs &a;
     const void *xs;  // vectors the search reads (float32 or bfloat16)
     int lane;
-    int *gvis;
+    unsigned *gbits;
+    int *glog;
     u64 *gpool;
     float4 qv[V];
+    RegList<1> head;  // the nearest candidates, sorted
+    RegList<KR> res;
     // per-query state, uniform across the warp
-    int ns, ng, cnt, ndc, nexp, nvis, nvis_g, kk, nscan, gcap;
+    int nh, no, ng, cnt, ndc, nexp, nvis, nlog, kk, nscan, es;
+    int pf_node, pf_id;  // adjacency row already loaded for the next expansion
     unsigned flags;
-    bool spill, rset, stop;
+    bool spill, rset, stop, padded;
     float r2;
     u64 tau;  // every key in the global pool is >= tau (kMaxKey when it is empty)
     double f2, bound2;
 
-    __device__ Warp(WarpSmem<HV> &s, const SearchArgs &args, const void *x, int ln, int *gv, u64 *gp)
-        : sm(s), a(args), xs(x), lane(ln), gvis(gv), gpool(gp)
+    __device__ Warp(WarpSmem<HV> &s, const SearchArgs &args, const void *x, int ln, unsigned *gb, int *gl, u64 *gp)
+        : sm(s), a(args), xs(x), lane(ln), gbits(gb), glog(gl), gpool(gp)
     {
     }
 
@@ -239,56 +316,31 @@ template <int V, class T, int HV> struct Warp {
             }
             h = (h + 1) & (HV - 1);
         }
-        return gvisit(gvis + gcap, gcap, id) == 1;
+        const unsigned bit = 1u << (id & 31);
+        return (atomicOr(&gbits[id >> 5], bit) & bit) == 0;
     }
 
-    // Insert into a spill table of `cap` slots at `tab`: 1 inserted, 0 present.
-    __device__ int gvisit(int *tab, int cap, int id)
-    {
-        unsigned hg = hash_id(id) >> (32 - __ffs(cap) + 1);
-        for (int t = 0; t < cap; ++t) {
-            int old = atomicCAS(&tab[hg], -1, id);
-            if (old == -1)
-                return 1;
-            if (old == id)
-                return 0;
-            hg = (hg + 1) & (cap - 1);
-        }
-        return 1;  // unreachable: tables are kept below half load
-    }
-
-    // Clears a spill table of `cap` slots at offset cap of the region.
-    __device__ void gclear(int cap)
-    {
-        int4 m1 = make_int4(-1, -1, -1, -1);
-        int4 *g4 = reinterpret_cast<int4 *>(gvis + cap);
-        for (int i = lane; i < cap / 4; i += 32)
-            g4[i] = m1;
-        __syncwarp();
-    }
-
-    // Starts the spill table when the shared table nears 3/4 load, and doubles
-    // the spill table (tables of size c live at offset c, so they never overlap)
-    // before a batch could take it past half load.
+    // Past half load of the shared table, new ids go to the bitmap.
     __device__ void begin_batch()
     {
-        if (!spill && nvis >= HV / 4 * 3 - 32) {
+        if (!spill && nvis >= HV / 2 - 32)
             spill = true;
-            gcap = kSpillFirst;
-            gclear(gcap);
+    }
+
+    // Leaves the bitmap all zero for the next query: clears the logged words,
+    // or the whole bitmap if the log overflowed.
+    __device__ void clear_bits()
+    {
+        if (!spill)
+            return;
+        if (nlog <= kVisitLog) {
+            for (int i = lane; i < nlog; i += 32)
+                gbits[glog[i] >> 5] = 0u;
+        } else {
+            for (int64_t i = lane; i < a.bits_words; i += 32)
+                gbits[i] = 0u;
         }
-        if (spill && nvis_g + 32 >= gcap / 2 && gcap * 2 <= kGlobalVisit / 2) {
-            const int ncap = gcap * 2;
-            gclear(ncap);
-            const int *old = gvis + gcap;
-            for (int i = lane; i < gcap; i += 32) {
-                int v = old[i];
-                if (v != -1)
-                    gvisit(gvis + ncap, ncap, v);
-            }
-            __syncwarp();
-            gcap = ncap;
-        }
+        __syncwarp();
     }
 
     // ---------------------------------------------------------------- distances
@@ -299,23 +351,27 @@ template <int V, class T, int HV> struct Warp {
         float mine = 0.0f;
         const int chunks = a.d >> 2;
         while (mask) {
+            // slot g takes the g-th id of the mask; every slot loads (empty slots
+            // read row 0 and are masked), so all loads issue back to back
             int src[G];
             int gid[G];
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 src[g] = mask ? __ffs(mask) - 1 : -1;
-                if (mask)
-                    mask &= mask - 1;
-                gid[g] = __shfl_sync(0xffffffffu, id, src[g] < 0 ? 0 : src[g]);
+                mask &= mask - 1;
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const int sid = __shfl_sync(FULL, id, src[g] < 0 ? 0 : src[g]);
+                gid[g] = (src[g] < 0 || sid < 0) ? 0 : sid;
             }
             float4 xv[G][V];
 #pragma unroll
             for (int g = 0; g < G; ++g)
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
-                    int c = lane + 32 * v;
-                    xv[g][v] = (src[g] >= 0 && c < chunks) ? L::load(base, gid[g], a.d, c)
-                                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const int c = lane + 32 * v;
+                    xv[g][v] = L::load(base, gid[g], a.d, c < chunks ? c : 0);
                 }
             float acc[G];
 #pragma unroll
@@ -331,7 +387,7 @@ template <int V, class T, int HV> struct Warp {
             float red = transpose_reduce<G>(acc, lane);
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-                float s = __shfl_sync(0xffffffffu, red, holder_lane<G>(g));
+                float s = __shfl_sync(FULL, red, holder_lane<G>(g));
                 if (lane == src[g])
                     mine = s;
             }
@@ -341,67 +397,23 @@ template <int V, class T, int HV> struct Warp {
 
     // ---------------------------------------------------------------- result list
 
-    // Inserts key into the sorted result list, keeping at most kk entries.
     __device__ void r_insert(u64 key)
     {
-        int pos = 0;
-#pragma unroll
-        for (int s = 0; s < kMaxK / 32; ++s) {
-            int i = s * 32 + lane;
-            pos += __popc(__ballot_sync(0xffffffffu, i < cnt && sm.res[i] < key));
-        }
+        const int pos = res.rank(key);
         if (pos >= kk)
             return;
-        int last = min(cnt, kk - 1);  // entries [pos, last) move up by one
-        u64 t[kMaxK / 32];
-#pragma unroll
-        for (int s = 0; s < kMaxK / 32; ++s) {
-            int i = s * 32 + lane;
-            if (i >= pos && i < last)
-                t[s] = sm.res[i];
-        }
-        __syncwarp();
-#pragma unroll
-        for (int s = 0; s < kMaxK / 32; ++s) {
-            int i = s * 32 + lane;
-            if (i >= pos && i < last)
-                sm.res[i + 1] = t[s];
-        }
-        if (lane == 0)
-            sm.res[pos] = key;
-        __syncwarp();
+        res.insert_at(pos, key, lane, kk);
         cnt = min(cnt + 1, kk);
     }
 
-    __device__ void update_bound()
-    {
-        bound2 = (rset && !isinf(f2)) ? (double)r2 * f2 : INFINITY;
-    }
+    __device__ void update_bound() { bound2 = (rset && !isinf(f2)) ? (double)r2 * f2 : INFINITY; }
 
     // ---------------------------------------------------------------- candidate pool
 
-    // Drops shared-pool entries beyond the bound.
-    __device__ void pool_compact()
-    {
-        int w = 0;
-        for (int base = 0; base < ns; base += 32) {
-            int i = base + lane;
-            u64 kv = i < ns ? sm.pool[i] : kMaxKey;
-            bool keep = i < ns && in_bound(kv);
-            unsigned km = __ballot_sync(0xffffffffu, keep);
-            __syncwarp();
-            if (keep)
-                sm.pool[w + __popc(km & lanemask_lt(lane))] = kv;
-            w += __popc(km);
-            __syncwarp();
-        }
-        ns = w;
-    }
-
-    // Appends `count` keys (one per lane in `mask`) to the global pool.
+    // Appends the keys of the lanes with `put` to the global pool.
     __device__ void gpool_append(bool put, u64 key)
     {
-        unsigned m = __ballot_sync(0xffffffffu, put);
+        unsigned m = __ballot_sync(FULL, put);
         if (!m)
             return;
         if (put) {
@@ -414,76 +426,87 @@ template <int V, class T, int HV> struct Warp {
         ng = min(ng + __popc(m), kGlobalPool);
     }
 
-    // Moves the farther half of the (full) shared pool to the global pool.
-    __device__ void spill_half()
+    // Makes room in the full overflow: drops its out-of-bound keys; if all are in
+    // bound, sorts it and moves the farther half to the global pool.
+    __device__ void make_room()
     {
-        constexpr int N = kPool / 32;
+        int w = 0;
+        for (int base = 0; base < no; base += 32) {
+            const int e = base + lane;
+            const u64 kv = e < no ? sm.ovf[e] : kMaxKey;
+            const bool keep = e < no && in_bound(kv);
+            const unsigned km = __ballot_sync(FULL, keep);
+            __syncwarp();
+            if (keep)
+                sm.ovf[w + __popc(km & lanemask_lt(lane))] = kv;
+            w += __popc(km);
+            __syncwarp();
+        }
+        no = w;
+        if (no < kOvf)
+            return;
+        constexpr int N = kOvf / 32;
         u64 v[N];
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-            int e = i * 32 + lane;
-            v[i] = e < ns ? sm.pool[e] : kMaxKey;
-        }
+        for (int i = 0; i < N; ++i)
+            v[i] = sm.ovf[i * 32 + lane];
         warp_bitonic_sort<N>(v, lane);
-        constexpr int keep = kPool / 2;
         __syncwarp();
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-            int e = i * 32 + lane;
-            if (e < keep && e < ns)
-                sm.pool[e] = v[i];
-        }
-        u64 first_moved = __shfl_sync(0xffffffffu, v[keep / 32], 0);
+        for (int i = 0; i < N / 2; ++i)
+            sm.ovf[i * 32 + lane] = v[i];
+        const u64 first_moved = __shfl_sync(FULL, v[N / 2], 0);
 #pragma unroll
-        for (int i = keep / 32; i < N; ++i) {
-            int e = i * 32 + lane;
-            gpool_append(e < ns, v[i]);
-        }
+        for (int i = N / 2; i < N; ++i)
+            gpool_append(true, v[i]);
         __syncwarp();
-        if (ns > keep) {
-            tau = first_moved;
-            ns = keep;
-        }
+        tau = first_moved;
+        no = kOvf / 2;
     }
 
-    // Refills the empty shared pool with the nearest in-bound global entries.
-    __device__ void refill()
+    __device__ void ovf_append(u64 key)
     {
-        constexpr int M = kPool / 2;  // entries brought back
-        u64 v[16];
+        if (no == kOvf)
+            make_room();
+        if (key >= tau) {
+            gpool_append(lane == 0, key);
+            return;
+        }
+        if (lane == 0)
+            sm.ovf[no] = key;
+        ++no;
+        __syncwarp();
+    }
+
+    // Refills the empty overflow with the 64 nearest in-bound global keys.
+    __device__ void refill_ovf()
+    {
+        u64 v[8];  // v[0..1]: best 64 so far; v[2..5]: next 128 global keys
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
+        for (int i = 0; i < 8; ++i)
             v[i] = kMaxKey;
-        for (int base = 0; base < ng; base += 256) {
+        for (int base = 0; base < ng; base += 128) {
 #pragma unroll
-            for (int i = 4; i < 12; ++i) {
-                int e = base + (i - 4) * 32 + lane;
+            for (int i = 2; i < 6; ++i) {
+                int e = base + (i - 2) * 32 + lane;
                 u64 kv = e < ng ? gpool[e] : kMaxKey;
                 v[i] = (kv != kMaxKey && in_bound(kv)) ? kv : kMaxKey;
             }
-#pragma unroll
-            for (int i = 12; i < 16; ++i)
-                v[i] = kMaxKey;
-            warp_bitonic_sort<16>(v, lane);  // the M smallest end up in v[0..3]
+            v[6] = v[7] = kMaxKey;
+            warp_bitonic_sort<8>(v, lane);
         }
-        const u64 kth = __shfl_sync(0xffffffffu, v[(M - 1) / 32], 31);
-        int m = 0;
-#pragma unroll
-        for (int i = 0; i < M / 32; ++i) {
-            int e = i * 32 + lane;
-            bool has = v[i] != kMaxKey;
-            if (has)
-                sm.pool[e] = v[i];
-            m += __popc(__ballot_sync(0xffffffffu, has));
-        }
-        // keep the global entries that are beyond kth and still in bound
+        const u64 kth = __shfl_sync(FULL, v[1], 31);
+        sm.ovf[lane] = v[0];
+        sm.ovf[32 + lane] = v[1];
+        no = __popc(__ballot_sync(FULL, v[0] != kMaxKey)) + __popc(__ballot_sync(FULL, v[1] != kMaxKey));
+        // keep the global entries beyond kth that are still in bound
         int w = 0;
         u64 mn = kMaxKey;
         for (int base = 0; base < ng; base += 32) {
             int e = base + lane;
             u64 kv = e < ng ? gpool[e] : kMaxKey;
             bool keep = e < ng && kv > kth && in_bound(kv);
-            unsigned km = __ballot_sync(0xffffffffu, keep);
+            unsigned km = __ballot_sync(FULL, keep);
             __syncwarp();
             if (keep) {
                 gpool[w + __popc(km & lanemask_lt(lane))] = kv;
@@ -494,101 +517,129 @@ template <int V, class T, int HV> struct Warp {
         }
         ng = w;
         tau = warp_min_u64(mn);
-        ns = m;
         __syncwarp();
     }
 
-    // Adds the batch members marked `push` to S.
+    // Refills the empty head with the 32 nearest in-bound overflow keys.
+    __device__ void refill_head()
+    {
+        if (no == 0) {
+            if (ng == 0)
+                return;
+            refill_ovf();
+        }
+        constexpr int N = kOvf / 32;
+        u64 v[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const int e = i * 32 + lane;
+            const u64 kv = e < no ? sm.ovf[e] : kMaxKey;
+            v[i] = (kv != kMaxKey && in_bound(kv)) ? kv : kMaxKey;
+        }
+        warp_bitonic_sort<N>(v, lane);
+        head.v[0] = v[0];
+        nh = __popc(__ballot_sync(FULL, v[0] != kMaxKey));
+        int m = 0;
+#pragma unroll
+        for (int i = 1; i < N; ++i)
+            m += __popc(__ballot_sync(FULL, v[i] != kMaxKey));
+        __syncwarp();
+#pragma unroll
+        for (int i = 1; i < N; ++i)
+            if ((i - 1) * 32 + lane < m)
+                sm.ovf[(i - 1) * 32 + lane] = v[i];
+        no = m;
+        __syncwarp();
+    }
+
+    // Adds the batch members marked `push` to S (one at a time; typically a few).
     __device__ void pool_push(bool push, u64 key)
     {
-        bool to_s = push && key < tau;
-        unsigned sm_mask = __ballot_sync(0xffffffffu, to_s);
-        int nps = __popc(sm_mask);
-        if (ns + nps > kPool) {
-            pool_compact();
-            if (ns + nps > kPool) {
-                spill_half();
-                to_s = push && key < tau;
-                sm_mask = __ballot_sync(0xffffffffu, to_s);
-                nps = __popc(sm_mask);
+        unsigned pm = __ballot_sync(FULL, push);
+        while (pm) {
+            const int src = __ffs(pm) - 1;
+            pm &= pm - 1;
+            const u64 ck = __shfl_sync(FULL, key, src);
+            if (ck >= tau) {
+                gpool_append(lane == 0, ck);
+                continue;
+            }
+            const u64 hmax = nh > 0 ? __shfl_sync(FULL, head.v[0], nh - 1) : kMaxKey;
+            const bool only_head = no == 0 && ng == 0;
+            if (ck < hmax || (only_head && nh < 32)) {
+                if (nh == 32)
+                    ovf_append(hmax);  // the evicted maximum stays >= the rest of the head
+                head.insert_at(head.rank(ck), ck, lane, 32);
+                nh = min(nh + 1, 32);
+            } else {
+                ovf_append(ck);
             }
         }
-        if (to_s)
-            sm.pool[ns + __popc(sm_mask & lanemask_lt(lane))] = key;
-        ns += nps;
-        gpool_append(push && !to_s, key);
-        __syncwarp();
     }
 
-    // Warp-wide min of the shared pool; removes and returns it.
+    // Removes and returns the minimum of S (the head's first key); refills the
+    // head when it runs empty.
     __device__ u64 pool_pop()
     {
-        u64 best = kMaxKey;
-        int bx = -1;
-        for (int i = lane; i < ns; i += 32) {
-            u64 kv = sm.pool[i];
-            if (kv < best) {
-                best = kv;
-                bx = i;
-            }
-        }
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) {
-            u64 ob = __shfl_xor_sync(0xffffffffu, best, off);
-            int ox = __shfl_xor_sync(0xffffffffu, bx, off);
-            if (ob < best) {
-                best = ob;
-                bx = ox;
-            }
-        }
-        __syncwarp();
-        if (lane == 0)
-            sm.pool[bx] = sm.pool[ns - 1];
-        --ns;
-        __syncwarp();
-        return best;
+        const u64 top = __shfl_sync(FULL, head.v[0], 0);
+        head.pop_front(lane);
+        --nh;
+        if (nh == 0 && (no > 0 || ng > 0))
+            refill_head();
+        return top;
     }
 
     // ---------------------------------------------------------------- one batch
 
     // Tests a batch of up to 32 ids (one per lane, -1 = none) and applies it.
-    __device__ void batch(int id, bool init)
+    // With `predict`, loads the adjacency row of the node expanded next.
+    __device__ void batch(int id, bool init, bool predict)
     {
         begin_batch();
         bool isnew = id >= 0 && visit(id);
-        unsigned mask = __ballot_sync(0xffffffffu, isnew);
+        unsigned mask = __ballot_sync(FULL, isnew);
         if (!mask)
             return;
         int nnew = __popc(mask);
         ndc += nnew;
-        if (spill)
-            nvis_g += nnew;
-        else
+        if (spill) {
+            const int pos = nlog + __popc(mask & lanemask_lt(lane));
+            if (isnew && pos < kVisitLog)
+                glog[pos] = id;
+            nlog += nnew;
+        } else {
             nvis += nnew;
+        }
         __syncwarp();
         float d2 = distances<Loader<T>>(xs, id, mask);
         u64 key = pack_key(d2, id);
+        if (predict) {
+            // next pop = min(S head, nearest batch member if it is pushed)
+            const u64 bmin = warp_min_u64(isnew ? key : kMaxKey);
+            const u64 top = __shfl_sync(FULL, head.v[0], 0);
+            const u64 next = ((double)key_d2(bmin) <= bound2 && bmin < top) ? bmin : top;
+            if (next != kMaxKey) {
+                pf_node = key_id(next);
+                pf_id = lane < es ? a.adj[(int64_t)pf_node * a.adj_w + lane] : -1;
+            }
+        }
         // R <- the best kk of R and the batch
-        unsigned cm = __ballot_sync(0xffffffffu, isnew && (init || !rset || d2 <= r2));
+        unsigned cm = __ballot_sync(FULL, isnew && (init || !rset || d2 <= r2));
         while (cm) {
             int src = __ffs(cm) - 1;
             cm &= cm - 1;
-            u64 ck = __shfl_sync(0xffffffffu, key, src);
+            u64 ck = __shfl_sync(FULL, key, src);
             if (init || !rset || key_d2(ck) <= r2) {
                 r_insert(ck);
                 if (!init && cnt == kk) {
                     rset = true;
-                    r2 = key_d2(sm.res[kk - 1]);
+                    r2 = key_d2(res.get(kk - 1));
                 }
             }
         }
         update_bound();
         // S <- S + batch members within r(1+eps)
         pool_push(isnew && (double)d2 <= bound2, key);
-        if (nvis_g + 32 >= gcap / 2 && gcap * 2 > kGlobalVisit / 2) {
-            flags |= ONNG_FLAG_VISIT_OVERFLOW;
-            stop = true;
-        }
     }
 
     __device__ void run(int64_t q)
@@ -601,15 +652,18 @@ template <int V, class T, int HV> struct Warp {
             qv[v] = c < (d >> 2) ? __ldg(reinterpret_cast<const float4 *>(qp) + c) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         const float eps = a.eps_q ? a.eps_q[q] : a.eps;
-        int es = a.es_q ? a.es_q[q] : a.e_s;
+        es = a.es_q ? a.es_q[q] : a.e_s;
         if (es <= 0)
             es = INT_MAX;
-        const bool padded = a.adj != nullptr && es <= a.adj_w;
+        padded = a.adj != nullptr && es <= a.adj_w;
+        const bool predict = padded && es <= 32;
         f2 = isinf(eps) ? INFINITY : (1.0 + (double)eps) * (1.0 + (double)eps);
         for (int i = lane; i < HV; i += 32)
             sm.vis[i] = -1;
-        ns = ng = cnt = ndc = nexp = nvis = nvis_g = nscan = 0;
-        gcap = kSpillFirst;
+        head.clear();
+        res.clear();
+        nh = no = ng = cnt = ndc = nexp = nvis = nlog = nscan = 0;
+        pf_node = -1;
         kk = a.k;
         flags = 0;
         spill = rset = stop = false;
@@ -624,14 +678,12 @@ template <int V, class T, int HV> struct Warp {
                 if (id >= a.n)
                     id = -1;
             }
-            batch(id < 0 ? -1 : id, true);
+            batch(id < 0 ? -1 : id, true, false);
         }
         while (!stop) {
-            if (ns == 0) {
-                if (ng == 0)
-                    break;
-                refill();
-                if (ns == 0)
+            if (nh == 0) {
+                refill_head();
+                if (nh == 0)
                     break;
             }
             const u64 sk = pool_pop();
@@ -643,18 +695,19 @@ template <int V, class T, int HV> struct Warp {
             }
             ++nexp;
             const int s = key_id(sk);
-            if (padded) {
-                // first `es` entries of the padded row; -1 marks the end of a short row
-                int id = lane < es ? a.adj[(int64_t)s * a.adj_w + lane] : -1;
-                nscan += __popc(__ballot_sync(0xffffffffu, id >= 0));
-                batch(id, false);
-                for (int c0 = 32; c0 < es && !stop; c0 += 32) {
-                    id = c0 + lane < es ? a.adj[(int64_t)s * a.adj_w + c0 + lane] : -1;
-                    unsigned got = __ballot_sync(0xffffffffu, id >= 0);
+            if (predict) {
+                const int id = s == pf_node ? pf_id : (lane < es ? a.adj[(int64_t)s * a.adj_w + lane] : -1);
+                pf_node = -1;
+                nscan += __popc(__ballot_sync(FULL, id >= 0));
+                batch(id, false, true);
+            } else if (padded) {
+                for (int c0 = 0; c0 < es && !stop; c0 += 32) {
+                    const int id = c0 + lane < es ? a.adj[(int64_t)s * a.adj_w + c0 + lane] : -1;
+                    const unsigned got = __ballot_sync(FULL, id >= 0);
                     if (!got)
                         break;
                     nscan += __popc(got);
-                    batch(id, false);
+                    batch(id, false, false);
                 }
             } else {
                 const int64_t beg = a.row_ptr[s];
@@ -663,7 +716,7 @@ template <int V, class T, int HV> struct Warp {
                 nscan += m;
                 for (int c0 = 0; c0 < m && !stop; c0 += 32) {
                     int id = c0 + lane < m ? a.col[beg + c0 + lane] : -1;
-                    batch(id, false);
+                    batch(id, false, false);
                 }
             }
         }
@@ -672,28 +725,38 @@ template <int V, class T, int HV> struct Warp {
     // Rescores the kept list in float32 against X and keeps the best k_out.
     __device__ void rerank()
     {
-        const int m = cnt;
-        for (int c0 = 0; c0 < m; c0 += 32) {
-            int i = c0 + lane;
-            int id = i < m ? key_id(sm.res[i]) : -1;
-            unsigned mask = __ballot_sync(0xffffffffu, id >= 0);
-            float dv = distances<Loader<float>>(a.X, id, mask);
-            if (id >= 0)
-                sm.pool[i] = pack_key(dv, id);
+        u64 nk[KR];
+#pragma unroll
+        for (int i = 0; i < KR; ++i) {
+            const int id = res.v[i] == kMaxKey ? -1 : key_id(res.v[i]);
+            const unsigned mask = __ballot_sync(FULL, id >= 0);
+            const float dv = distances<Loader<float>>(a.X, id, mask);
+            nk[i] = id >= 0 ? pack_key(dv, id) : kMaxKey;
         }
-        __syncwarp();
+        res.clear();
         cnt = 0;
         kk = a.k_out;
-        for (int i = 0; i < m; ++i)
-            r_insert(sm.pool[i]);
+#pragma unroll
+        for (int i = 0; i < KR; ++i) {
+            unsigned m = __ballot_sync(FULL, nk[i] != kMaxKey);
+            while (m) {
+                const int src = __ffs(m) - 1;
+                m &= m - 1;
+                r_insert(__shfl_sync(FULL, nk[i], src));
+            }
+        }
     }
 
     __device__ void write(int64_t q)
     {
         const int k = a.k_out;
-        for (int i = lane; i < k; i += 32) {
-            a.out_ids[q * k + i] = i < cnt ? key_id(sm.res[i]) : -1;
-            a.out_dist[q * k + i] = i < cnt ? sqrtf(key_d2(sm.res[i])) : INFINITY;
+#pragma unroll
+        for (int i = 0; i < KR; ++i) {
+            const int e = i * 32 + lane;
+            if (e < k) {
+                a.out_ids[q * k + e] = e < cnt ? key_id(res.v[i]) : -1;
+                a.out_dist[q * k + e] = e < cnt ? sqrtf(key_d2(res.v[i])) : INFINITY;
+            }
         }
         if (a.stats && lane == 0) {
             a.stats[q * 4 + 0] = ndc;
@@ -704,8 +767,12 @@ template <int V, class T, int HV> struct Warp {
     }
 };
 
-template <int V, class T, int HV>
-__global__ void __launch_bounds__(kWarpsPerCta * 32) search_kernel(SearchArgs a)
+// Resident CTAs per SM the register budget is sized for (no spills at these
+// counts; shared memory allows 7 CTAs of 4 warps with the 2048-slot table).
+__host__ __device__ constexpr int min_blocks(int V, int KR) { return V <= 2 && KR == 1 ? 4 : 3; }
+
+template <int V, class T, int HV, int KR>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, min_blocks(V, KR)) search_kernel(SearchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto *smem = reinterpret_cast<WarpSmem<HV> *>(smem_raw);
@@ -713,15 +780,17 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) search_kernel(SearchArgs a)
     const int lane = threadIdx.x & 31;
     const int64_t slot = (int64_t)blockIdx.x * kWarpsPerCta + warp;
     const void *xs = std::is_same<T, float>::value ? static_cast<const void *>(a.X) : static_cast<const void *>(a.Xb);
-    Warp<V, T, HV> w(smem[warp], a, xs, lane, a.gvis + slot * kGlobalVisit, a.gpool + slot * kGlobalPool);
+    Warp<V, T, HV, KR> w(smem[warp], a, xs, lane, a.gbits + slot * a.bits_words, a.glog + slot * kVisitLog,
+                         a.gpool + slot * kGlobalPool);
     for (;;) {
         int q = 0;
         if (lane == 0)
             q = atomicAdd(a.counter, 1);
-        q = __shfl_sync(0xffffffffu, q, 0);
+        q = __shfl_sync(FULL, q, 0);
         if (q >= a.nq)
             break;
         w.run(q);
+        w.clear_bits();
         if (!std::is_same<T, float>::value)
             w.rerank();
         w.write(q);
@@ -746,22 +815,25 @@ struct Launch {
     size_t smem;
 };
 
-template <int V, class T> Launch pick()
+template <int V, class T> Launch pick_kr(int k)
 {
-    return {search_kernel<V, T, ONNG_SEARCH_HV>, sizeof(WarpSmem<ONNG_SEARCH_HV>) * kWarpsPerCta};
+    constexpr size_t sm = sizeof(WarpSmem<ONNG_SEARCH_HV>) * kWarpsPerCta;
+    if (k <= 32)
+        return {search_kernel<V, T, ONNG_SEARCH_HV, 1>, sm};
+    return {search_kernel<V, T, ONNG_SEARCH_HV, kMaxK / 32>, sm};
 }
 
-template <class T> Launch pick_v(int d)
+template <class T> Launch pick_v(int d, int k)
 {
     const int V = (d + 127) / 128;
     if (V <= 1)
-        return pick<1, T>();
+        return pick_kr<1, T>(k);
     if (V <= 2)
-        return pick<2, T>();
+        return pick_kr<2, T>(k);
     if (V <= 4)
-        return pick<4, T>();
+        return pick_kr<4, T>(k);
     if (V <= 8)
-        return pick<8, T>();
+        return pick_kr<8, T>(k);
     return {nullptr, 0};
 }
 
@@ -778,7 +850,12 @@ int resident_blocks(const Launch &L, int *per_sm)
     return ONNG_OK;
 }
 
-constexpr size_t kSlotBytes = (size_t)kGlobalVisit * sizeof(int) + (size_t)kGlobalPool * sizeof(u64);
+// per-warp workspace: visited bitmap (rounded to 256 bytes), id log, candidate spill pool
+int64_t bits_words(int64_t n) { return (n + 8191) / 8192 * 256; }
+size_t slot_bytes(int64_t n)
+{
+    return (size_t)bits_words(n) * sizeof(unsigned) + (size_t)kVisitLog * sizeof(int) + (size_t)kGlobalPool * sizeof(u64);
+}
 
 }  // namespace
 }  // namespace onng
@@ -787,14 +864,13 @@ using namespace onng;
 
 extern "C" size_t onng_search_workspace_bytes(int64_t nq, const onng_index *idx, const onng_search_params *p)
 {
-    (void)p;
-    Launch L = pick_v<float>(idx ? idx->d : 128);
+    Launch L = pick_v<float>(idx ? idx->d : 128, p ? std::max(p->k, p->k_rerank) : 10);
     int per_sm = 16;
     if (!L.fn || resident_blocks(L, &per_sm) != ONNG_OK)
         per_sm = 16;
     const int64_t blocks = std::min<int64_t>(std::max<int64_t>(1, (nq + kWarpsPerCta - 1) / kWarpsPerCta),
                                              (int64_t)per_sm * num_sms());
-    return 256 + (size_t)blocks * kWarpsPerCta * kSlotBytes;
+    return 1024 + (size_t)blocks * kWarpsPerCta * slot_bytes(idx ? idx->n : 1);
 }
 
 extern "C" int onng_pad_adjacency(const int64_t *row_ptr, const int32_t *col, int64_t n, int32_t width, int32_t *adj,
@@ -839,7 +915,7 @@ extern "C" int onng_search(const onng_index *idx, const float *Q, int64_t nq, co
     ONNG_REQUIRE(aligned16(idx->X) && aligned16(Q), ONNG_E_INVAL, "onng_search: X and Q must be 16-byte aligned");
     ONNG_REQUIRE(ws, ONNG_E_WORKSPACE, "onng_search: NULL workspace");
 
-    Launch L = bf16 ? pick_v<__nv_bfloat16>(idx->d) : pick_v<float>(idx->d);
+    Launch L = bf16 ? pick_v<__nv_bfloat16>(idx->d, kr) : pick_v<float>(idx->d, kr);
     ONNG_REQUIRE(L.fn, ONNG_E_UNSUPPORTED, "onng_search: no kernel for d=%d", idx->d);
     int per_sm = 0;
     int st = resident_blocks(L, &per_sm);
@@ -847,16 +923,20 @@ extern "C" int onng_search(const onng_index *idx, const float *Q, int64_t nq, co
         return st;
     int64_t blocks = std::min<int64_t>((nq + kWarpsPerCta - 1) / kWarpsPerCta, (int64_t)per_sm * num_sms());
     // the workspace bounds the number of warps (each needs its own spill tables)
-    const int64_t fit = ws_bytes > 256 ? (int64_t)((ws_bytes - 256) / (kSlotBytes * kWarpsPerCta)) : 0;
+    const size_t per_cta = slot_bytes(idx->n) * kWarpsPerCta;
+    const int64_t fit = ws_bytes > 1024 ? (int64_t)((ws_bytes - 1024) / per_cta) : 0;
     blocks = std::min(blocks, fit);
     ONNG_REQUIRE(blocks >= 1, ONNG_E_WORKSPACE, "onng_search: workspace of %zu bytes holds no CTA (%zu needed per CTA)",
-                 ws_bytes, kSlotBytes * kWarpsPerCta + 256);
+                 ws_bytes, per_cta + 1024);
 
     WsCarver c(ws);
     SearchArgs a;
     a.counter = c.take<int>(64);
-    a.gvis = c.take<int>((size_t)blocks * kWarpsPerCta * kGlobalVisit);
-    a.gpool = c.take<u64>((size_t)blocks * kWarpsPerCta * kGlobalPool);
+    const int64_t slots = blocks * kWarpsPerCta;
+    a.bits_words = bits_words(idx->n);
+    a.gbits = c.take<unsigned>((size_t)slots * a.bits_words);
+    a.glog = c.take<int>((size_t)slots * kVisitLog);
+    a.gpool = c.take<u64>((size_t)slots * kGlobalPool);
     a.row_ptr = idx->row_ptr;
     a.col = idx->col;
     a.adj = idx->adj;
@@ -881,6 +961,9 @@ extern "C" int onng_search(const onng_index *idx, const float *Q, int64_t nq, co
     a.stats = stats;
     cudaStream_t s = to_cuda(stream);
     ONNG_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(int), s), "onng_search: reset counter");
+    // the bitmaps start empty; every query leaves its bitmap empty again
+    ONNG_CUDA_TRY(cudaMemsetAsync(a.gbits, 0, sizeof(unsigned) * (size_t)slots * a.bits_words, s),
+                  "onng_search: clear visited bitmaps");
     L.fn<<<(unsigned)blocks, kWarpsPerCta * 32, L.smem, s>>>(a);
     return check_launch("onng_search");
 }

@@ -271,15 +271,16 @@ def test_pad_adjacency(onng, sift_graph):
 
 
 def test_search_visited_spill(onng):
-    """A query that visits more nodes than the shared-memory table holds spills to
-    the global table and still matches the oracle."""
+    """Queries that visit more nodes than the shared-memory table holds continue in
+    the global bitmap and still match the oracle; the warps reuse their bitmaps
+    for later queries, so a wrong clear would show up as missing visits."""
     X, Q = synth.workload("sift1m", n=10000, nq=20)
     nbr, ln = onng.build_knng(dev(X), 40)
     g = onng.adjust_degree(nbr, ln, 20, 40)
     seeds = onng.seeds_pivot(dev(X), dev(Q), 256, 10)
     ids, dist, st = onng.search(onng.Index(g[0], g[1], dev(X)), dev(Q), 100, 0, 0.5, seeds)
     o_ids, _, o_st = oracle.search(host(g[0]), host(g[1]), X, Q, 100, 0, np.float32(0.5), host(seeds))
-    assert host(st)[:, 2].max() > 3072
+    assert (host(st)[:, 0] > 2048).sum() >= 5
     assert np.array_equal(host(ids), o_ids)
     assert np.array_equal(host(st)[:, 0], o_st[:, 0])
 
