@@ -3,25 +3,30 @@
 Workload: n = 1,000,000 SIFT-like integer descriptors (d = 128, values 0..255
 stored float32, ~30 % zeros, 1,000 clusters), 10,000 held-out queries from the
 same mixture, exact kNN graph k = 100, degree adjustment (e_o, e_i), path
-adjustment, nearest-pivot seeds, top-10.
+adjustment, nearest-pivot seeds, top-10.  Synthetic stand-in for SIFT1M.
 
-A step is one pass of the search path over the 10,000-query batch: seed
-selection and the search kernel, on inputs already resident in HBM.  The global
-eps of each search form is first calibrated (bisection) so that mean recall@10
-against exact ground truth is >= 0.95.  The vectors (512 MB) exceed the 129 MB
-L2, and L2 is also flushed between timed steps.
-
-Forms timed: plain float32 search and the bfloat16 pass with float32 rerank.
-`value` is the bfloat16 form's queries/s; the float32 form is reported beside it.
+A step is one pass of the search path over the 10,000-query batch on inputs
+already resident in HBM.  Three forms are timed, each at the operating point
+where mean recall@10 against exact ground truth is >= 0.95:
+  fp32     plain search, one global eps (bisection), fixed e_s
+  bf16     the same with bfloat16 vectors and a float32 rerank of k_rerank
+  learned  bf16 search with per-query (eps, e_s) from the predictor network:
+           probe (first h hops) -> bfloat16 network -> search; the network is
+           trained on the GPU first, on cost-aware labels of 20,000 training
+           queries, and its price lambda is calibrated by bisection
+`value` is the learned+bf16 form; the plain fp32 form is reported beside it.
+The vectors (512 MB) exceed the 129 MB L2, and L2 is also flushed between
+timed steps.
 
 Launch: python bench.py [--gpus N --steps K --warmup W] (torchrun for N > 1: each
 rank searches its own replica; no collective on the data path).
 --impl reference: the CPU oracle's search (Algorithm 1 in plain C, OpenMP over
-the host cores) on the same index and queries.
+the host cores) on the same index, queries and fp32 operating point.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -48,6 +53,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--nq", type=int, default=10_000)
+    ap.add_argument("--ntrain", type=int, default=20_000)
     ap.add_argument("--k", type=int, default=10)
     ap.add_argument("--knn-k", type=int, default=100)
     ap.add_argument("--e-o", type=int, default=20)
@@ -57,6 +63,8 @@ def parse():
     ap.add_argument("--n-seed", type=int, default=10)
     ap.add_argument("--target", type=float, default=0.95)
     ap.add_argument("--k-rerank", type=int, default=20)
+    ap.add_argument("--probe-hops", type=int, default=8)
+    ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--eps-fp32", type=float, default=None, help="use this eps instead of calibrating")
     ap.add_argument("--eps-bf16", type=float, default=None, help="use this eps instead of calibrating")
     ap.add_argument("--no-adj", action="store_true", help="read adjacency from CSR, not the padded table")
@@ -116,10 +124,8 @@ class Clocks:
 
 
 def recall_at(ids, gt):
-    import torch
-    k = gt.shape[1]
     hit = (ids[:, :, None] == gt[:, None, :]) & (gt[:, None, :] >= 0)
-    return float(hit.any(2).sum(1).float().mean().item() / k)
+    return float(hit.any(2).sum(1).float().mean().item() / gt.shape[1])
 
 
 def build_index(onng, torch, Xd, a):
@@ -137,6 +143,7 @@ def build_index(onng, torch, Xd, a):
     idx = onng.Index(p[0], p[1], Xd, None, p[2])
     if not a.no_adj:
         idx.with_adjacency(a.e_s)
+    idx.with_bf16()
     info = {"knng_s": round(t1 - t0, 3), "degree_s": round(t2 - t1, 4), "path_s": round(t3 - t2, 4),
             "edges_degree": int(g[0][-1]), "edges_path": int(p[0][-1])}
     del nbr, ln, g
@@ -160,6 +167,17 @@ def calibrate(run, gt, target, lo=0.0, hi=1.0, iters=12):
     return hi
 
 
+def search_bytes(st, d, a, vec_bytes, rerank):
+    """Algorithmic bytes of one search launch: gathered vectors, adjacency entries
+    scanned, one 16-byte row header per expansion, queries, seeds and outputs."""
+    st = st.cpu().numpy().astype(np.float64)
+    b = st[:, 0].sum() * d * vec_bytes + st[:, 2].sum() * 4 + st[:, 1].sum() * 16
+    b += a.nq * d * 4 + a.nq * a.n_seed * 4 + a.nq * a.k * 8
+    if rerank:
+        b += a.nq * a.k_rerank * d * 4
+    return b, float(st[:, 0].mean())
+
+
 def main():
     a = parse()
     import torch
@@ -174,10 +192,10 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    from paper_1810_07355_gb300 import onng, synth
+    from paper_1810_07355_gb300 import learned, onng, synth
     onng.load()
-    X, Q = synth.workload("sift1m", n=a.n, nq=a.nq)
-    Xd, Qd = torch.from_numpy(X).to(dev), torch.from_numpy(Q).to(dev)
+    X, Q, Qtr = synth.workload("sift1m", n=a.n, nq=a.nq, train=a.ntrain)
+    Xd, Qd, Qtrd = (torch.from_numpy(x).to(dev) for x in (X, Q, Qtr))
     idx, build = build_index(onng, torch, Xd, a)
     gt, _ = onng.knn(Xd, Qd, a.k)
     seeds = onng.seeds_pivot(Xd, Qd, a.n_pivot, a.n_seed)
@@ -189,111 +207,135 @@ def main():
         return onng.search(idx, Qd, a.k, a.e_s, eps, seeds, precision=onng.PREC_BF16, k_rerank=a.k_rerank)
 
     eps32 = a.eps_fp32 if a.eps_fp32 is not None else calibrate(run32, gt, a.target)
-    eps16 = a.eps_bf16 if a.eps_bf16 is not None else calibrate(run16, gt, a.target)
     config = {"workload": f"sift-like n={a.n} d=128 int0-255 fp32, {a.nq} queries, top-{a.k}",
-              "knng_k": a.knn_k, "e_o": a.e_o, "e_i": a.e_i, "e_s": a.e_s, "seeds": f"{a.n_seed} nearest of "
-              f"{a.n_pivot} pivots", "eps_fp32": round(eps32, 5), "eps_bf16": round(eps16, 5),
+              "knng_k": a.knn_k, "e_o": a.e_o, "e_i": a.e_i, "e_s": a.e_s,
+              "seeds": f"{a.n_seed} nearest of {a.n_pivot} pivots", "eps_fp32": round(eps32, 5),
               "k_rerank": a.k_rerank, "l2": "inputs 512 MB > L2 and L2 flushed between steps",
-              "adjacency": "csr" if a.no_adj else f"padded first {a.e_s}",
-              "parallelism": f"replicas x{world}"}
-
+              "adjacency": "csr" if a.no_adj else f"padded first {a.e_s}", "parallelism": f"replicas x{world}"}
     if a.impl == "reference":
-        reference_arm(a, idx, X, Q, seeds, gt, eps32, config, world)
+        reference_arm(a, idx, X, Q, seeds, eps32, config, world)
         return
+
+    eps16 = a.eps_bf16 if a.eps_bf16 is not None else calibrate(run16, gt, a.target)
+    # the learned form: labels, GPU training, alpha calibration (all untimed preparation)
+    t0 = time.perf_counter()
+    gt_tr, _ = onng.knn(Xd, Qtrd, a.k)
+    seeds_tr = onng.seeds_pivot(Xd, Qtrd, a.n_pivot, a.n_seed)
+    pred, _ = learned.train(idx, Qtrd, gt_tr, seeds_tr, a.k, h=a.probe_hops, steps=a.train_steps)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    t_pred = learned.calibrate_lambda(pred, idx, Qd, gt, seeds, a.k, a.target, k_rerank=a.k_rerank)
+    alpha = 1.0
+    config.update({"eps_bf16": round(eps16, 5), "probe_hops": a.probe_hops, "train_queries": a.ntrain,
+                   "log10_lambda": round(t_pred, 4), "train_s": round(t_train, 2),
+                   "final_train_loss": round(float(np.mean(pred.losses[-50:])), 4)})
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def timed(run, eps, steps):
-        """Per-step device times (ms): whole step and the search kernel alone."""
-        step_ms, kern_ms, st = [], [], None
+    def step(form):
+        """One step; returns (ids, stats, event before the search kernel)."""
+        s = onng.seeds_pivot(Xd, Qd, a.n_pivot, a.n_seed)
+        if form == "learned":
+            feat, _ = onng.search_probe(idx, Qd, a.k, pred.probe_es, pred.probe_eps, s, pred.h, t_pred)
+            eq, es = onng.mlp_predict(pred.P, feat, alpha, pred.es_min, pred.es_max)
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(stream)
+            ids, _, st = onng.search(idx, Qd, a.k, pred.es_max, 0.0, s, precision=onng.PREC_BF16,
+                                     k_rerank=a.k_rerank, eps_q=eq, es_q=es)
+            return ids, st, e
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        if form == "fp32":
+            ids, _, st = onng.search(idx, Qd, a.k, a.e_s, eps32, s)
+        else:
+            ids, _, st = onng.search(idx, Qd, a.k, a.e_s, eps16, s, precision=onng.PREC_BF16, k_rerank=a.k_rerank)
+        return ids, st, e
+
+    def timed(form, steps):
+        step_ms, kern_ms, out = [], [], None
         for _ in range(steps):
             flush.fill_(1)
-            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            s = onng.seeds_pivot(Xd, Qd, a.n_pivot, a.n_seed)
-            e1.record(stream)
-            ids, dist, st = (run16 if run == "bf16" else run32)(eps)
+            ids, st, e1 = step(form)
             e2.record(stream)
             e2.synchronize()
             step_ms.append(e0.elapsed_time(e2))
             kern_ms.append(e1.elapsed_time(e2))
-        return step_ms, kern_ms, st, ids
+            out = (ids, st)
+        return step_ms, kern_ms, out
 
-    for form, eps in (("fp32", eps32), ("bf16", eps16)):
-        timed(form, eps, a.warmup)
+    forms = ("fp32", "bf16", "learned")
+    for f in forms:
+        timed(f, a.warmup)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     res = {}
     with Clocks(local) as clk:
         t0 = time.perf_counter()
-        for form, eps in (("fp32", eps32), ("bf16", eps16)):
-            step_ms, kern_ms, st, ids = timed(form, eps, a.steps)
-            res[form] = dict(step_ms=step_ms, kern_ms=kern_ms, st=st, ids=ids)
+        for f in forms:
+            res[f] = timed(f, a.steps)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     if world > 1:
         torch.distributed.barrier()
     clocks = clk.summary()
 
-    def agg(form):
-        ms = float(np.mean(res[form]["step_ms"]))
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    def agg(f):
+        t = torch.tensor([float(np.mean(res[f][0]))], dtype=torch.float64, device=dev)
         if world > 1:
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item())
 
-    ms32, ms16 = agg("fp32"), agg("bf16")
-    qps32 = world * a.nq / (ms32 / 1e3)
-    qps16 = world * a.nq / (ms16 / 1e3)
-    rec32 = recall_at(res["fp32"]["ids"], gt)
-    rec16 = recall_at(res["bf16"]["ids"], gt)
-
-    # roofline of the dominant kernel (the search of the headline form)
+    ms = {f: agg(f) for f in forms}
+    qps = {f: world * a.nq / (ms[f] / 1e3) for f in forms}
+    rec = {f: recall_at(res[f][2][0], gt) for f in forms}
+    d = X.shape[1]
     peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
-    st = res["bf16"]["st"].cpu().numpy().astype(np.float64)
-    d = X.shape[1]
-    bytes16 = (st[:, 0].sum() * d * 2 + st[:, 2].sum() * 4 + st[:, 1].sum() * 16 + a.nq * d * 4
-               + a.nq * a.k_rerank * d * 4 + a.nq * a.k * 8 + a.nq * a.n_seed * 4)
-    kern16 = float(np.mean(res["bf16"]["kern_ms"])) / 1e3
-    st32 = res["fp32"]["st"].cpu().numpy().astype(np.float64)
-    bytes32 = (st32[:, 0].sum() * d * 4 + st32[:, 2].sum() * 4 + st32[:, 1].sum() * 16 + a.nq * d * 4
-               + a.nq * a.k * 8 + a.nq * a.n_seed * 4)
-    kern32 = float(np.mean(res["fp32"]["kern_ms"])) / 1e3
+    kern = {f: float(np.mean(res[f][1])) / 1e3 for f in forms}
+    byt, ndc = {}, {}
+    for f in forms:
+        byt[f], ndc[f] = search_bytes(res[f][2][1], d, a, 4 if f == "fp32" else 2, f != "fp32")
     traffic = None
     if os.path.exists(TRAFFIC):
         tr = json.load(open(TRAFFIC))
-        import hashlib
         src = open(os.path.join(ROOT, "paper_1810_07355_gb300", "csrc", "search.cu"), "rb").read()
-        if tr.get("search_src_sha256") == hashlib.sha256(src).hexdigest():
-            traffic = tr.get("bf16_bytes_per_query", None)
-            traffic = None if traffic is None else traffic * a.nq
-    roof = {"bound": "hbm", "achieved": round(bytes16 / kern16 / 1e9, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(bytes16 / kern16 / 1e9 / peak, 4), "traffic": traffic,
-            "kernel": "search_kernel (bf16 + fp32 rerank)", "peak_source": "measured hbm_gbs (burst)",
-            "fp32_kernel": {"achieved": round(bytes32 / kern32 / 1e9, 1),
-                            "frac": round(bytes32 / kern32 / 1e9 / peak, 4)}}
+        if tr.get("search_src_sha256") == hashlib.sha256(src).hexdigest() and tr.get("bytes_per_query"):
+            traffic = tr["bytes_per_query"] * a.nq
+    roof = {"bound": "hbm", "achieved": round(byt["learned"] / kern["learned"] / 1e9, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(byt["learned"] / kern["learned"] / 1e9 / peak, 4), "traffic": traffic,
+            "kernel": "search_kernel (learned per-query eps/e_s, bf16 + fp32 rerank)",
+            "peak_source": "measured hbm_gbs (burst), MEASURED_PEAKS.json",
+            "per_form": {f: {"achieved_gbs": round(byt[f] / kern[f] / 1e9, 1),
+                             "frac": round(byt[f] / kern[f] / 1e9 / peak, 4),
+                             "search_kernel_ms": round(kern[f] * 1e3, 3),
+                             "algorithmic_bytes": int(byt[f])} for f in forms}}
 
-    e2e = end_to_end(onng, torch, a, idx, Q, eps16, dev)
+    e2e = end_to_end(onng, torch, a, idx, Q, pred, t_pred, alpha, dev)
     cpu = cpu_baseline(a, idx, X, Q, seeds, eps32) if rank == 0 and world == 1 else None
     if rank == 0:
-        line = {"metric": METRIC, "value": round(qps16, 1), "unit": "queries/s", "n_gpus": world,
-                "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms16, 4), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate, fp32 rerank)",
+        line = {"metric": METRIC, "value": round(qps["learned"], 1), "unit": "queries/s", "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms["learned"], 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16 (fp32 accumulate, fp32 rerank; predictor bf16)",
                 "data": "synthetic (seeded SIFT-like mixture; no dataset on the box)", "config": config,
-                "recall_at_10": {"bf16": round(rec16, 4), "fp32": round(rec32, 4)},
-                "plain_fp32": {"value": round(qps32, 1), "ms_per_step": round(ms32, 4)},
-                "learned": "not built yet: value is the fixed-eps bf16 form",
-                "dist_computations_per_query": {"bf16": float(st[:, 0].mean()), "fp32": float(st32[:, 0].mean())},
-                "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": 2 * a.steps * 2,
-                "clocks": clocks, "build": build, "wall_s_timed_region": round(wall, 3)}
+                "recall_at_10": {f: round(rec[f], 4) for f in forms},
+                "plain_fp32": {"value": round(qps["fp32"], 1), "ms_per_step": round(ms["fp32"], 4)},
+                "fixed_eps_bf16": {"value": round(qps["bf16"], 1), "ms_per_step": round(ms["bf16"], 4)},
+                "learned_over_plain_fp32": round(qps["learned"] / qps["fp32"], 3),
+                "dist_computations_per_query": {f: round(ndc[f], 1) for f in forms},
+                "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,
+                "gpu_launches": a.steps * (2 + 2 + 4), "clocks": clocks, "build": build,
+                "wall_s_timed_region": round(wall, 3)}
         print(json.dumps(line), flush=True)
 
 
-def end_to_end(onng, torch, a, idx, Q, eps, dev):
-    """Same metric through the public API with host buffers: H2D of the queries, seeds + search, D2H of results."""
+def end_to_end(onng, torch, a, idx, Q, pred, t_pred, alpha, dev):
+    """The learned+bf16 form through the public API with host buffers: H2D of the
+    queries, seeds, probe, predictor and search, D2H of ids and distances."""
     pin_q = torch.from_numpy(Q).pin_memory()
     out_ids = torch.empty((a.nq, a.k), dtype=torch.int32).pin_memory()
     out_d = torch.empty((a.nq, a.k), dtype=torch.float32).pin_memory()
@@ -302,8 +344,10 @@ def end_to_end(onng, torch, a, idx, Q, eps, dev):
     def step():
         q = pin_q.to(dev, non_blocking=True)
         s = onng.seeds_pivot(idx.X, q, a.n_pivot, a.n_seed)
-        ids, dist, _ = onng.search(idx, q, a.k, a.e_s, eps, s, precision=onng.PREC_BF16, k_rerank=a.k_rerank,
-                                   stats=False)
+        feat, _ = onng.search_probe(idx, q, a.k, pred.probe_es, pred.probe_eps, s, pred.h, t_pred)
+        eq, es = onng.mlp_predict(pred.P, feat, alpha, pred.es_min, pred.es_max)
+        ids, dist, _ = onng.search(idx, q, a.k, pred.es_max, 0.0, s, precision=onng.PREC_BF16, k_rerank=a.k_rerank,
+                                   eps_q=eq, es_q=es, stats=False)
         out_ids.copy_(ids, non_blocking=True)
         out_d.copy_(dist, non_blocking=True)
 
@@ -318,7 +362,7 @@ def end_to_end(onng, torch, a, idx, Q, eps, dev):
     e1.synchronize()
     ms = e0.elapsed_time(e1) / a.steps
     return {"value": round(a.nq / (ms / 1e3), 1), "unit": "queries/s", "h2d_bytes_per_step": a.nq * Q.shape[1] * 4,
-            "d2h_bytes_per_step": a.nq * a.k * 8}
+            "d2h_bytes_per_step": a.nq * a.k * 8, "form": "learned+bf16"}
 
 
 def cpu_baseline(a, idx, X, Q, seeds, eps, sample=2000):
@@ -334,10 +378,10 @@ def cpu_baseline(a, idx, X, Q, seeds, eps, sample=2000):
     oracle.search(ptr, col, X, Q[:m], a.k, a.e_s, float(np.float32(eps)), s[:m], threads=cores)
     dt = time.perf_counter() - t0
     return {"value": round(m / dt, 1), "unit": "queries/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {m} of the {len(Q)} queries, same index, seeds and fp32 eps"}
+            "sample": f"first {m} of the {len(Q)} queries, same index, seeds and fp32 eps (plain form)"}
 
 
-def reference_arm(a, idx, X, Q, seeds, gt, eps, config, world):
+def reference_arm(a, idx, X, Q, seeds, eps, config, world):
     """Times the CPU oracle's search (the reference for this build) on the host cores."""
     import oracle
     oracle.build()
@@ -350,8 +394,8 @@ def reference_arm(a, idx, X, Q, seeds, gt, eps, config, world):
     for i in range(a.warmup + a.steps):
         lo = (i * per_step) % len(Q)
         t0 = time.perf_counter()
-        ids, _, _ = oracle.search(ptr, col, X, Q[lo:lo + per_step], a.k, a.e_s, float(np.float32(eps)),
-                                  s[lo:lo + per_step], threads=cores)
+        oracle.search(ptr, col, X, Q[lo:lo + per_step], a.k, a.e_s, float(np.float32(eps)), s[lo:lo + per_step],
+                      threads=cores)
         if i >= a.warmup:
             times.append(time.perf_counter() - t0)
     ms = 1e3 * float(np.mean(times))
@@ -362,7 +406,7 @@ def reference_arm(a, idx, X, Q, seeds, gt, eps, config, world):
             "impl": "reference",
             "cpu_baseline": {"value": v, "unit": "queries/s", "cores": cores, "kind": "oracle",
                              "sample": f"{per_step} queries per step of the {len(Q)}; index built on the GPU "
-                                       "and checked against the oracle stepwise; fp32 operating eps"},
+                                       "and checked against the oracle stepwise; plain fp32 operating eps"},
             "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -44,7 +44,7 @@ enum onng_status {
 /* per-query flags, stats[q*4 + 3] */
 #define ONNG_FLAG_S_OVERFLOW 1u      /* candidate pool full: farthest candidates dropped */
 #define ONNG_FLAG_VISIT_OVERFLOW 2u  /* reserved (the visited set cannot overflow) */
-#define ONNG_FLAG_LIMIT 4u           /* max_expansions reached */
+#define ONNG_FLAG_LIMIT 4u           /* stopped by max_expansions with an in-bound candidate left */
 
 const char *onng_last_error(void);
 int onng_version(void);
@@ -176,9 +176,56 @@ int onng_search(const onng_index *idx, const float *Q, int64_t nq, const onng_se
                 int32_t *out_ids, float *out_dist, int32_t *stats, void *ws, size_t ws_bytes,
                 onng_stream_t stream);
 
+/* Probe for the learned parameter predictor: runs the search with
+ * p->max_expansions (>= 1) as the number of hops h and writes, per query,
+ * features [nq, 16] float32 instead of results:
+ *   0 target (copied),  1 log d_s1,  2 log(d_s2/d_s1),  3 log(mean seed dist/d_s1),
+ *   4 log(r_1/d_s1),  5 log(r_k/r_1),  6 log(next/r_1),  7 new nodes / nodes scanned,
+ *   8 expansions / h,  9 log(1 + distance computations),  10 result insertions /
+ *   distance computations,  11 R full,  12 log(r_k/d_s1),  13 log(1 + scanned),
+ *   14 capped with an in-bound candidate left,  15 log(d)/8,
+ * where d_s1, d_s2 are the two nearest seed distances, r_1 / r_k the first / last
+ * of R after the h hops, and `next` the nearest candidate left, capped at
+ * r(1+eps) (equal to it when the search ended).  Distances are Euclidean.
+ * The paper's counterpart is Eq. 1, a fixed function of eps. */
+int onng_search_probe(const onng_index *idx, const float *Q, int64_t nq, const onng_search_params *p,
+                      const int32_t *seeds, int32_t n_seed, float target, float *features, int32_t *stats,
+                      void *ws, size_t ws_bytes, onng_stream_t stream);
+
 /* adj [n, width]: the first `width` entries of every CSR row, -1 past its end */
 int onng_pad_adjacency(const int64_t *row_ptr, const int32_t *col, int64_t n, int32_t width,
                        int32_t *adj, onng_stream_t stream);
+
+/* ------------------------------------------------------- parameter predictor
+ * A 16 -> 64 -> 64 -> 2 network with ReLU hidden layers mapping probe features
+ * to (log(eps + 0.01), log e_s) per query (no paper counterpart; it replaces the
+ * fixed policy of Eq. 1).  P is the flat float32 parameter vector
+ * W1[64][16], b1[64], W2[64][64], b2[64], W3[2][64], b3[2] (onng_mlp_nparam()
+ * values); X [B, 16] float32 rows; targets T [B, 2].
+ *   onng_mlp_forward:   Y [B, 2] = network(X) in float32.
+ *   onng_mlp_loss_grad: loss (1 float) = mean over B of 0.5 * |Y - T|^2, and
+ *                       G [nparam] its gradient (G and loss are overwritten).
+ *   onng_mlp_adam:      one Adam step (Kingma & Ba 2015) on P with moments M, V
+ *                       at step count t >= 1.
+ *   onng_mlp_train:     `steps` Adam steps (lr, beta 0.9 / 0.999, eps 1e-8) on
+ *                       consecutive mini-batches of `batch` <= 128 rows of X / T
+ *                       (wrapping), steps numbered t0 + 1 ...; G is unused
+ *                       (may be NULL); losses [steps] (optional) receives each
+ *                       loss.  Runs in one CTA.
+ *   onng_mlp_predict:   bfloat16 evaluation (weights and inputs rounded to
+ *                       bfloat16, float32 accumulation): eps_out = max(0,
+ *                       exp(y0) - 0.01) * alpha, es_out = clamp(round(exp(y1)),
+ *                       es_min, es_max). */
+int onng_mlp_nparam(void);
+int onng_mlp_forward(const float *P, const float *X, int64_t B, float *Y, onng_stream_t stream);
+int onng_mlp_loss_grad(const float *P, const float *X, const float *T, int64_t B, float *G, float *loss,
+                       onng_stream_t stream);
+int onng_mlp_adam(float *P, const float *G, float *M, float *V, int64_t t, float lr, float beta1,
+                  float beta2, float eps, onng_stream_t stream);
+int onng_mlp_train(float *P, float *M, float *V, const float *X, const float *T, int64_t N, int32_t batch,
+                   int64_t steps, int64_t t0, float lr, float *G, float *losses, onng_stream_t stream);
+int onng_mlp_predict(const float *P, const float *X, int64_t B, float alpha, int32_t es_min,
+                     int32_t es_max, float *eps_out, int32_t *es_out, onng_stream_t stream);
 
 /* float32 -> bfloat16 (round to nearest even) copy of a vector set, for X_bf16 */
 int onng_to_bf16(const float *X, int64_t count, uint16_t *out, onng_stream_t stream);

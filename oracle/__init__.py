@@ -67,6 +67,9 @@ def _load():
             lib.oracle_search.argtypes = [vp, vp, vp, i64, i32, vp, i64, i32, i32, dbl, vp, i32,
                                           vp, vp, vp, i32]
             lib.oracle_search.restype = i32
+            lib.oracle_search_probe.argtypes = [vp, vp, vp, i64, i32, vp, i64, i32, i32, dbl, vp, i32,
+                                                i64, dbl, vp, vp, i32]
+            lib.oracle_search_probe.restype = i32
             lib.oracle_bf16_round.argtypes = [vp, i64, vp]
             lib.oracle_bf16_round.restype = None
             lib.oracle_mlp_nparam.restype = i32
@@ -225,6 +228,23 @@ def search(ptr, col, X, Q, k: int, e_s: int, eps: float, seeds, threads: int = 0
                                _p(seeds), seeds.shape[1], _p(ids), _p(dist), _p(stats), threads)
     assert rc == 0, rc
     return ids, dist, stats
+
+
+def search_probe(ptr, col, X, Q, k: int, e_s: int, eps: float, seeds, h: int, target: float, threads: int = 0):
+    """Algorithm 1 stopped after h expansions; returns (features float64 [nq,16], stats int64 [nq,4])."""
+    ptr = _c(ptr, np.int64)
+    col = _c(col, np.int32)
+    X = _c(X, np.float32)
+    Q = _c(Q, np.float32)
+    seeds = _c(seeds, np.int32)
+    n, d = X.shape
+    nq = Q.shape[0]
+    feat = np.empty((nq, 16), np.float64)
+    stats = np.empty((nq, 4), np.int64)
+    rc = _load().oracle_search_probe(_p(ptr), _p(col), _p(X), n, d, _p(Q), nq, k, e_s, float(eps), _p(seeds),
+                                     seeds.shape[1], h, float(target), _p(feat), _p(stats), threads)
+    assert rc == 0, rc
+    return feat, stats
 
 
 def bf16_round(x):

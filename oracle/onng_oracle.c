@@ -20,6 +20,8 @@
  *   oracle_adjust_path_alg4  Algorithm 4 taken literally (round-robin, ascending ids)
  *   oracle_search         KnnSearch, Algorithm 1, with the visited set of
  *                         Algorithms Set/IsSet (Sec. 2.5) and e_p of Eq. 1 as e_s
+ *   oracle_search_probe   Algorithm 1 stopped after h expansions, with the features
+ *                         the learned (eps, e_s) predictor reads (no paper counterpart)
  *   oracle_seeds_random   random seed rule (the paper's "rand" seeds, Sec. 3)
  *   oracle_seeds_pivot    nearest-pivot seed rule (stands in for the vp-tree
  *                         seeds of Sec. 2 / Table 5, which the paper leaves unspecified)
@@ -581,9 +583,10 @@ int oracle_hash_selftest(const int32_t *ids, int64_t m, int64_t n, uint8_t *was_
  * stats [nq, 4]: distance computations, expansions (nodes popped and scanned),
  * largest |S|, flags (0).
  */
-int oracle_search(const int64_t *ptr, const int32_t *col, const float *X, int64_t n, int d,
-                  const float *Q, int64_t nq, int k, int e_s, double eps, const int32_t *seeds,
-                  int n_seed, int32_t *out_ids, double *out_dist, int64_t *stats, int threads)
+static int search_core(const int64_t *ptr, const int32_t *col, const float *X, int64_t n, int d,
+                       const float *Q, int64_t nq, int k, int e_s, double eps, const int32_t *seeds,
+                       int n_seed, int32_t *out_ids, double *out_dist, int64_t *stats, int threads,
+                       int64_t max_exp, double target, double *feat)
 {
     if (k <= 0 || d <= 0 || n <= 0 || n_seed <= 0)
         return ORACLE_E_INVAL;
@@ -614,8 +617,9 @@ int oracle_search(const int64_t *ptr, const int32_t *col, const float *X, int64_
                 continue;
             const float *q = Q + qi * (int64_t)d;
             visited_clear(&vis);
-            int64_t ns = 0, nr = 0, maxs = 0, ndc = 0, nexp = 0;
-            double r = INFINITY;
+            int64_t ns = 0, nr = 0, maxs = 0, ndc = 0, nexp = 0, nscan = 0, rins = 0, nseed = 0;
+            double r = INFINITY, seed_sum = 0.0;
+            int capped = 0;
             /* S <- Seed(G), R <- S (k nearest), C <- seeds */
             for (int t = 0; t < n_seed; ++t) {
                 int32_t sd = seeds[qi * (int64_t)n_seed + t];
@@ -631,6 +635,17 @@ int oracle_search(const int64_t *ptr, const int32_t *col, const float *X, int64_
                 S[ns].d = dv;
                 S[ns].id = sd;
                 ++ns;
+                ++nseed;
+                seed_sum += dv;
+            }
+            double ds1 = INFINITY, ds2 = INFINITY; /* two nearest seed distances */
+            for (int64_t t = 0; t < ns; ++t) {
+                if (S[t].d < ds1) {
+                    ds2 = ds1;
+                    ds1 = S[t].d;
+                } else if (S[t].d < ds2) {
+                    ds2 = S[t].d;
+                }
             }
             for (int64_t t = 0; t < ns; ++t) {
                 /* R keeps the k nearest seeds: insert, evict the largest when |R| > k */
@@ -649,15 +664,20 @@ int oracle_search(const int64_t *ptr, const int32_t *col, const float *X, int64_
                 for (int64_t u = 1; u < ns; ++u)
                     if (lt_pair(S[u].d, S[u].id, S[a].d, S[a].id))
                         a = u;
+                double bound = isinf(eps) ? INFINITY : r * (1.0 + eps);
+                if (max_exp > 0 && nexp >= max_exp) { /* probe: stop after max_exp hops */
+                    capped = S[a].d <= bound;
+                    break;
+                }
                 cand_t s = S[a];
                 S[a] = S[--ns];
-                double bound = isinf(eps) ? INFINITY : r * (1.0 + eps);
                 if (s.d > bound)
                     break;
                 ++nexp;
                 int64_t p = 1;
                 for (int64_t t = ptr[s.id]; t < ptr[s.id + 1] && p <= e_lim; ++t, ++p) {
                     int32_t nb = col[t];
+                    ++nscan;
                     if (visited_isset(&vis, nb))
                         continue;
                     visited_set(&vis, nb);
@@ -679,13 +699,16 @@ int oracle_search(const int64_t *ptr, const int32_t *col, const float *X, int64_
                         R[nr].d = dn;
                         R[nr].id = nb;
                         ++nr;
+                        int survived = 1;
                         if (nr > k) {
                             int64_t b = 0;
                             for (int64_t u = 1; u < nr; ++u)
                                 if (lt_pair(R[b].d, R[b].id, R[u].d, R[u].id))
                                     b = u;
+                            survived = b != nr - 1;
                             R[b] = R[--nr];
                         }
+                        rins += survived;
                         if (nr == k) {
                             r = R[0].d;
                             for (int64_t u = 1; u < nr; ++u)
@@ -715,6 +738,39 @@ int oracle_search(const int64_t *ptr, const int32_t *col, const float *X, int64_
                 stats[qi * 4 + 2] = maxs;
                 stats[qi * 4 + 3] = 0;
             }
+            if (feat) {
+                /* features of the probe, in the order of the library's probe output */
+                const double e6 = 1e-6;
+                double *f = feat + qi * 16;
+                double s1 = nseed > 0 ? ds1 : 0.0, s2 = nseed > 1 ? ds2 : s1;
+                double dmean = nseed > 0 ? seed_sum / (double)nseed : s1;
+                double rb = nr > 0 ? R[0].d : s1, rk = nr > 0 ? R[nr - 1].d : s1;
+                double bound = (isinf(eps) || isinf(r)) ? INFINITY : r * (1.0 + eps);
+                double smin = INFINITY;
+                for (int64_t u = 0; u < ns; ++u)
+                    if (S[u].d < smin)
+                        smin = S[u].d;
+                double top = capped ? (smin < bound ? smin : bound) : bound;
+                if (isinf(top))
+                    top = rk;
+                int64_t denom7 = nseed + nscan > 0 ? nseed + nscan : 1;
+                f[0] = target;
+                f[1] = log(s1 + e6);
+                f[2] = log((s2 + e6) / (s1 + e6));
+                f[3] = log((dmean + e6) / (s1 + e6));
+                f[4] = log((rb + e6) / (s1 + e6));
+                f[5] = log((rk + e6) / (rb + e6));
+                f[6] = log((top + e6) / (rb + e6));
+                f[7] = (double)ndc / (double)denom7;
+                f[8] = (double)nexp / (double)(max_exp > 0 ? max_exp : 1);
+                f[9] = log1p((double)ndc);
+                f[10] = (double)rins / (double)(ndc > 0 ? ndc : 1);
+                f[11] = isinf(r) ? 0.0 : 1.0;
+                f[12] = log((rk + e6) / (s1 + e6));
+                f[13] = log1p((double)nscan);
+                f[14] = capped ? 1.0 : 0.0;
+                f[15] = log((double)d) / 8.0;
+            }
         }
         free(S);
         free(R);
@@ -722,6 +778,36 @@ int oracle_search(const int64_t *ptr, const int32_t *col, const float *X, int64_
             visited_free(&vis);
     }
     return err;
+}
+
+int oracle_search(const int64_t *ptr, const int32_t *col, const float *X, int64_t n, int d,
+                  const float *Q, int64_t nq, int k, int e_s, double eps, const int32_t *seeds,
+                  int n_seed, int32_t *out_ids, double *out_dist, int64_t *stats, int threads)
+{
+    return search_core(ptr, col, X, n, d, Q, nq, k, e_s, eps, seeds, n_seed, out_ids, out_dist,
+                       stats, threads, 0, 0.0, NULL);
+}
+
+/*
+ * The probe of the learned parameter predictor: Algorithm 1 stopped before the
+ * (h+1)-th expansion, with per-query features [nq, 16] of its state (the list
+ * and definitions are in the library header; this is their float64 form).
+ * "capped" means h expansions were done and the nearest candidate left lies
+ * within r(1+eps).
+ */
+int oracle_search_probe(const int64_t *ptr, const int32_t *col, const float *X, int64_t n, int d,
+                        const float *Q, int64_t nq, int k, int e_s, double eps, const int32_t *seeds,
+                        int n_seed, int64_t h, double target, double *feat, int64_t *stats, int threads)
+{
+    if (h < 1)
+        return ORACLE_E_INVAL;
+    int32_t *ids = (int32_t *)malloc((size_t)(nq > 0 ? nq : 1) * (size_t)k * sizeof(int32_t));
+    double *dist = (double *)malloc((size_t)(nq > 0 ? nq : 1) * (size_t)k * sizeof(double));
+    int rc = search_core(ptr, col, X, n, d, Q, nq, k, e_s, eps, seeds, n_seed, ids, dist, stats,
+                         threads, h, target, feat);
+    free(ids);
+    free(dist);
+    return rc;
 }
 
 /* ------------------------------------------------------- reduced precision (O5) */

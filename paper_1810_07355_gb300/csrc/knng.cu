@@ -20,6 +20,10 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "warp_sort.cuh"
 
@@ -75,10 +79,11 @@ __device__ __forceinline__ void load_slab(const float *__restrict__ M, int64_t r
     }
 }
 
-template <int KC>
+template <int KC, int NBUF = BUF>
 __device__ void merge_row(int r, int64_t grow, unsigned long long *__restrict__ best, unsigned long long *__restrict__ buf,
                           float *s_thr, int *s_cnt, int lane)
 {
+    static_assert(KC + NBUF <= 512, "merge sorts 512 keys");
     const int cnt = s_cnt[r];
     unsigned long long v[16];
 #pragma unroll
@@ -87,7 +92,7 @@ __device__ void merge_row(int r, int64_t grow, unsigned long long *__restrict__ 
         if (e < KC)
             v[i] = best[grow * KC + e];
         else if (e - KC < cnt)
-            v[i] = buf[grow * BUF + (e - KC)];
+            v[i] = buf[grow * NBUF + (e - KC)];
         else
             v[i] = EMPTY_KEY;
     }
@@ -257,6 +262,359 @@ __global__ void knn_final_kernel(const float *__restrict__ X, int d, const float
     }
 }
 
+// ---------------------------------------------------------------- tensor cores
+//
+// knn_tc_kernel: the same sweep with the dot products on the 5th-generation
+// tensor cores, for inputs that are exact in bfloat16 (integers in [-256, 256]
+// with squared norms below 2^24, e.g. 8-bit image descriptors): then every
+// product and partial sum is an integer below 2^24 and the float32
+// accumulation, hence the ranking, is exact.
+//
+// One CTA owns 128 query rows (the A operand, loaded once by TMA) and sweeps the
+// base in tiles of 256 rows (the B operand, a two-stage TMA ring).  Shared
+// memory holds both operands K-major in 128-byte-swizzled atoms (8 rows x 64
+// bfloat16).  Warp 9 allocates 512 TMEM columns (two 128 x 256 float32
+// accumulators); its lane 0 issues tcgen05.mma (M = 128, N = 256, K = 16 per
+// instruction) and commits to mbarriers that free the smem stage and hand the
+// accumulator to the epilogue.  Warp 8 lane 0 issues the TMA loads.  Warps 0-7
+// read the accumulators with tcgen05.ld (warp w sees TMEM lanes 32 (w % 4) ..
+// +31, i.e. one query row per thread, and columns 128 (w / 4) .. +127), form
+// |q|^2 + |x|^2 - 2 q.x, filter against the row's threshold and append to the
+// row's candidate buffer; rows whose buffer may not absorb another tile are
+// merged between tiles.  Every mbarrier wait gives up after 2 s, records an
+// error code and lets all roles reach the teardown, where TMEM is freed.
+constexpr int TC_M = 128, TC_N = 256, TC_BUF = 384, TC_STAGES = 2;
+constexpr int TC_EPI = 256;                 // epilogue threads (8 warps)
+constexpr int TC_THREADS = TC_EPI + 64;     // + TMA warp + MMA warp
+constexpr unsigned long long TC_TIMEOUT_NS = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait on a phase; false (and *err set) after TC_TIMEOUT_NS or when
+// another role has already given up.
+__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code)
+{
+    if (mbar_try_wait(bar, parity))
+        return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity))
+            return true;
+        if ((it & 63) == 0) {
+            if (*reinterpret_cast<volatile int *>(err) != 0)
+                return false;
+            if (global_ns() - t0 > TC_TIMEOUT_NS) {
+                atomicCAS(err, 0, code);
+                return false;
+            }
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int c0, int c1, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+// Shared-memory matrix descriptor: K-major operand in 128-byte-swizzled atoms of
+// 8 rows x 128 bytes stacked 1024 bytes apart (start address >> 4, leading
+// offset unused, stride offset 1024 >> 4, descriptor version 1, swizzle 128B).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+// Instruction descriptor, kind::f16: float32 accumulator, bfloat16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t umma_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
+                 "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+                 : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                 "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                 "[%32];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                   "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                   "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(TC_EPI) : "memory"); }
+
+template <int KA> struct TcSmem {
+    static constexpr int A_ATOM = TC_M * 128;   // bytes of one 64-wide K atom of A
+    static constexpr int B_ATOM = TC_N * 128;
+    static constexpr int A_BYTES = KA * A_ATOM;
+    static constexpr int B_STAGE = KA * B_ATOM;
+    // alignment slack, operands, then barriers, TMEM address, flags, thresholds, counts
+    static constexpr int BYTES = 1024 + A_BYTES + TC_STAGES * B_STAGE + 2048;
+};
+
+template <int KC, int KA>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n,
+                  int64_t nq, int64_t self_offset, const float *__restrict__ xn, const float *__restrict__ qn,
+                  unsigned long long *__restrict__ best, unsigned long long *__restrict__ buf, int *err)
+{
+    using L = TcSmem<KA>;
+    extern __shared__ unsigned char tc_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *sA = base;
+    unsigned char *sB = base + L::A_BYTES;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + TC_STAGES * L::B_STAGE);
+    uint64_t *full = bars, *empty = bars + TC_STAGES, *accf = bars + 2 * TC_STAGES, *acce = accf + 2, *abar = acce + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(abar + 1);
+    int *s_ok = reinterpret_cast<int *>(tmem_slot + 1);
+    float *s_thr = reinterpret_cast<float *>(s_ok + 4);
+    int *s_cnt = reinterpret_cast<int *>(s_thr + TC_M);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t row0 = (int64_t)blockIdx.x * TC_M;
+    const int64_t tiles = (n + TC_N - 1) / TC_N;
+
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], TC_EPI);
+        }
+        mbar_init(abar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 9) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int r = tid; r < TC_M; r += blockDim.x) {
+        s_thr[r] = INFINITY;
+        s_cnt[r] = 0;
+    }
+    for (int e = tid; e < TC_M * KC; e += blockDim.x) {
+        const int64_t gr = row0 + e / KC;
+        if (gr < nq)
+            best[gr * KC + e % KC] = EMPTY_KEY;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 8) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int64_t issued = 0;
+            mbar_expect_tx(abar, L::A_BYTES);
+            for (int a = 0; a < KA; ++a)
+                tma_load_2d(sA + a * L::A_ATOM, &tmA, a * 64, (int)row0, abar);
+            for (int64_t t = 0; t < tiles; ++t) {
+                const int s = (int)(t % TC_STAGES);
+                if (t >= TC_STAGES && !mbar_wait(&empty[s], (uint32_t)(((t / TC_STAGES) & 1) ^ 1), err, 1))
+                    break;
+                mbar_expect_tx(&full[s], L::B_STAGE);
+                for (int a = 0; a < KA; ++a)
+                    tma_load_2d(sB + s * L::B_STAGE + a * L::B_ATOM, &tmB, a * 64, (int)(t * TC_N), &full[s]);
+                issued = t + 1;
+            }
+            // our copies in flight complete before the CTA may exit (bounded)
+            int dummy = 0;
+            mbar_wait(abar, 0, &dummy, 6);
+            for (int64_t t = issued > TC_STAGES ? issued - TC_STAGES : 0; t < issued; ++t)
+                mbar_wait(&full[t % TC_STAGES], (uint32_t)((t / TC_STAGES) & 1), &dummy, 6);
+        }
+    } else if (warp == 9) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = umma_idesc(TC_M, TC_N);
+            int64_t done = 0;
+            bool ok = mbar_wait(abar, 0, err, 2);
+            for (int64_t t = 0; ok && t < tiles; ++t) {
+                const int s = (int)(t % TC_STAGES), b = (int)(t & 1);
+                if (!mbar_wait(&full[s], (uint32_t)((t / TC_STAGES) & 1), err, 3))
+                    break;
+                if (t >= 2 && !mbar_wait(&acce[b], (uint32_t)(((t >> 1) & 1) ^ 1), err, 4))
+                    break;
+                tc_fence_after();
+                const uint32_t aa = smem_u32(sA), bb = smem_u32(sB + s * L::B_STAGE);
+#pragma unroll
+                for (int kk = 0; kk < 4 * KA; ++kk) {
+                    const uint32_t off = (uint32_t)((kk & 3) * 32);  // 16 bf16 = 32 bytes inside the atom
+                    const uint64_t ad = umma_desc(aa + (kk >> 2) * L::A_ATOM + off);
+                    const uint64_t bd = umma_desc(bb + (kk >> 2) * L::B_ATOM + off);
+                    umma_bf16(tmem + (uint32_t)(b * TC_N), ad, bd, idesc, kk > 0 ? 1u : 0u);
+                }
+                umma_commit(&empty[s]);
+                umma_commit(&accf[b]);
+                done = t + 1;
+            }
+            // the MMAs issued so far complete before TMEM is freed (bounded)
+            int dummy = 0;
+            if (done > 0)
+                mbar_wait(&accf[(done - 1) & 1], (uint32_t)(((done - 1) >> 1) & 1), &dummy, 7);
+        }
+    } else {
+        // ------------------------------------------------ epilogue (warps 0-7)
+        const int qd = warp & 3, half = warp >> 2;
+        const int r = qd * 32 + lane;
+        const int64_t grow = row0 + r;
+        const bool row_ok = grow < nq;
+        const float qnr = row_ok ? qn[grow] : 0.f;
+        const int64_t self = (self_offset >= 0 && row_ok) ? self_offset + grow : -1;
+        float thr = INFINITY;
+        for (int64_t t = 0; t < tiles; ++t) {
+            const int b = (int)(t & 1);
+            if (tid == 0)
+                s_ok[0] = mbar_wait(&accf[b], (uint32_t)((t >> 1) & 1), err, 5) ? 1 : 0;
+            epi_sync();
+            if (!s_ok[0])
+                break;
+            tc_fence_after();
+            const int64_t col0 = t * TC_N + half * 128;
+#pragma unroll 1
+            for (int c = 0; c < 4; ++c) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * TC_N + half * 128 + c * 32), v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int64_t col = col0 + c * 32 + j;
+                    if (col < n && row_ok && col != self) {
+                        const float d2 = fmaxf(qnr + __ldg(xn + col) - 2.f * __uint_as_float(v[j]), 0.f);
+                        if (d2 < thr) {
+                            const int pos = atomicAdd(&s_cnt[r], 1);
+                            buf[grow * TC_BUF + pos] = pack_key(d2, (int)col);
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&acce[b]);
+            epi_sync();
+            const bool last = t + 1 == tiles;
+            for (int rr = warp; rr < TC_M; rr += TC_EPI / 32) {
+                const int64_t gr = row0 + rr;
+                if (gr >= nq)
+                    break;
+                const int cnt = s_cnt[rr];
+                if (cnt > TC_BUF - TC_N || (last && cnt > 0))
+                    merge_row<KC, TC_BUF>(rr, gr, best, buf, s_thr, s_cnt, lane);
+            }
+            epi_sync();
+            thr = s_thr[r];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 9) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    }
+}
+
+// Sets *flag if any of the values is not an integer in [-256, 256].
+__global__ void bf16_exact_kernel(const float *__restrict__ x, int64_t count, int *flag)
+{
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = x[i];
+        bad |= !(v == rintf(v) && fabsf(v) <= 256.f);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0)
+        atomicOr(flag, 1);
+}
+
+__global__ void f32_to_bf16_kernel(const float *__restrict__ x, int64_t count, __nv_bfloat16 *__restrict__ y)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = __float2bfloat16_rn(x[i]);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2-D bf16 tensor map over rows x d (row-major), box 64 x box_rows, 128B swizzle,
+// zero fill outside the matrix.
+int make_map(CUtensorMap *m, const void *ptr, int64_t rows, int d, int box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn)
+        return set_error(ONNG_E_CUDA, "onng_knn: cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)d * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return set_error(ONNG_E_CUDA, "onng_knn: tensor map encode failed (%d)", (int)r);
+    return ONNG_OK;
+}
+
 int pick_kc(int k)
 {
     for (int kc = 32; kc <= 256; kc <<= 1)
@@ -277,6 +635,63 @@ int launch(const float *X, int64_t n, int d, const float *Q, int64_t nq, int k, 
     return check_launch("onng_knn: final kernel");
 }
 
+template <int KC, int KA>
+int launch_tc_kc(const CUtensorMap &ma, const CUtensorMap &mb, int64_t n, int64_t nq, int64_t self_offset,
+                 const float *xn, const float *qn, unsigned long long *best, unsigned long long *bufp, int *err,
+                 cudaStream_t s)
+{
+    const size_t smem = TcSmem<KA>::BYTES;
+    ONNG_CUDA_TRY(cudaFuncSetAttribute(reinterpret_cast<const void *>(knn_tc_kernel<KC, KA>),
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                  "onng_knn: tensor kernel smem attribute");
+    knn_tc_kernel<KC, KA><<<(unsigned)((nq + TC_M - 1) / TC_M), TC_THREADS, smem, s>>>(ma, mb, n, nq, self_offset, xn,
+                                                                                     qn, best, bufp, err);
+    return check_launch("onng_knn: tensor kernel");
+}
+
+int launch_tc(const float *X, int64_t n, int d, const float *Q, int64_t nq, int k, int kc, int64_t self_offset,
+              int32_t *nbr, float *len, float *xn, float *qn, unsigned long long *best, unsigned long long *bufp,
+              int *err, __nv_bfloat16 *xb, __nv_bfloat16 *qb, cudaStream_t s)
+{
+    const int gb = num_sms() * 8;
+    f32_to_bf16_kernel<<<gb, 256, 0, s>>>(X, n * d, xb);
+    f32_to_bf16_kernel<<<gb, 256, 0, s>>>(Q, nq * d, qb);
+    int st = check_launch("onng_knn: bf16 copies");
+    if (st)
+        return st;
+    CUtensorMap ma, mb;
+    if ((st = make_map(&ma, qb, nq, d, TC_M)) || (st = make_map(&mb, xb, n, d, TC_N)))
+        return st;
+    const int ka = d / 64;
+    if (kc == 32)
+        st = ka == 1 ? launch_tc_kc<32, 1>(ma, mb, n, nq, self_offset, xn, qn, best, bufp, err, s)
+                     : launch_tc_kc<32, 2>(ma, mb, n, nq, self_offset, xn, qn, best, bufp, err, s);
+    else if (kc == 64)
+        st = ka == 1 ? launch_tc_kc<64, 1>(ma, mb, n, nq, self_offset, xn, qn, best, bufp, err, s)
+                     : launch_tc_kc<64, 2>(ma, mb, n, nq, self_offset, xn, qn, best, bufp, err, s);
+    else
+        st = ka == 1 ? launch_tc_kc<128, 1>(ma, mb, n, nq, self_offset, xn, qn, best, bufp, err, s)
+                     : launch_tc_kc<128, 2>(ma, mb, n, nq, self_offset, xn, qn, best, bufp, err, s);
+    if (st)
+        return st;
+    int code = 0;
+    ONNG_CUDA_TRY(cudaMemcpyAsync(&code, err, sizeof(int), cudaMemcpyDeviceToHost, s), "onng_knn: error flag");
+    ONNG_CUDA_TRY(cudaStreamSynchronize(s), "onng_knn: tensor kernel");
+    if (code)
+        return set_error(ONNG_E_LIMIT, "onng_knn: tensor-core pipeline wait timed out (role %d)", code);
+    switch (kc) {
+    case 32:
+        knn_final_kernel<32><<<(unsigned)((nq * 32 + 255) / 256), 256, 0, s>>>(X, d, Q, nq, best, k, nbr, len);
+        break;
+    case 64:
+        knn_final_kernel<64><<<(unsigned)((nq * 32 + 255) / 256), 256, 0, s>>>(X, d, Q, nq, best, k, nbr, len);
+        break;
+    default:
+        knn_final_kernel<128><<<(unsigned)((nq * 32 + 255) / 256), 256, 0, s>>>(X, d, Q, nq, best, k, nbr, len);
+    }
+    return check_launch("onng_knn: final kernel");
+}
+
 }  // namespace
 }  // namespace onng
 
@@ -284,13 +699,15 @@ using namespace onng;
 
 extern "C" size_t onng_knn_workspace_bytes(int64_t n, int32_t d, int64_t nq, int32_t k)
 {
-    (void)d;
     int kc = pick_kc(k);
     WsCarver c(nullptr);
     c.take<float>((size_t)std::max<int64_t>(n, 1));
     c.take<float>((size_t)std::max<int64_t>(nq, 1));
     c.take<unsigned long long>((size_t)std::max<int64_t>(nq, 1) * (kc ? kc : 32));
-    c.take<unsigned long long>((size_t)std::max<int64_t>(nq, 1) * BUF);
+    c.take<unsigned long long>((size_t)std::max<int64_t>(nq, 1) * std::max(BUF, TC_BUF));
+    c.take<int>(64);
+    c.take<__nv_bfloat16>((size_t)std::max<int64_t>(n, 1) * std::max(d, 1));
+    c.take<__nv_bfloat16>((size_t)std::max<int64_t>(nq, 1) * std::max(d, 1));
     return c.used;
 }
 
@@ -313,7 +730,10 @@ extern "C" int onng_knn(const float *X, int64_t n, int32_t d, const float *Q, in
     float *xn = c.take<float>((size_t)std::max<int64_t>(n, 1));
     float *qn = c.take<float>((size_t)nq);
     unsigned long long *best = c.take<unsigned long long>((size_t)nq * kc);
-    unsigned long long *bufp = c.take<unsigned long long>((size_t)nq * BUF);
+    unsigned long long *bufp = c.take<unsigned long long>((size_t)nq * std::max(BUF, TC_BUF));
+    int *flags = c.take<int>(64);
+    __nv_bfloat16 *xb = c.take<__nv_bfloat16>((size_t)std::max<int64_t>(n, 1) * d);
+    __nv_bfloat16 *qb = c.take<__nv_bfloat16>((size_t)nq * d);
     cudaStream_t s = to_cuda(stream);
     if (n > 0)
         norms_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(X, n, d, xn);
@@ -321,6 +741,18 @@ extern "C" int onng_knn(const float *X, int64_t n, int32_t d, const float *Q, in
     int st = check_launch("onng_knn: norms");
     if (st)
         return st;
+    // tensor-core path: d of 64 or 128, k + 16 <= 128, values exact in bfloat16
+    if (n > 0 && (d == 64 || d == 128) && kc <= 128 && n <= INT32_MAX - TC_N) {
+        ONNG_CUDA_TRY(cudaMemsetAsync(flags, 0, 64 * sizeof(int), s), "onng_knn: clear flags");
+        const int gb = num_sms() * 8;
+        bf16_exact_kernel<<<gb, 256, 0, s>>>(X, n * d, flags);
+        bf16_exact_kernel<<<gb, 256, 0, s>>>(Q, nq * d, flags);
+        int inexact = 1;
+        ONNG_CUDA_TRY(cudaMemcpyAsync(&inexact, flags, sizeof(int), cudaMemcpyDeviceToHost, s), "onng_knn: flag");
+        ONNG_CUDA_TRY(cudaStreamSynchronize(s), "onng_knn: exactness check");
+        if (!inexact)
+            return launch_tc(X, n, d, Q, nq, k, kc, self_offset, nbr, len, xn, qn, best, bufp, flags + 1, xb, qb, s);
+    }
     switch (kc) {
     case 32: return launch<32>(X, n, d, Q, nq, k, self_offset, nbr, len, xn, qn, best, bufp, s);
     case 64: return launch<64>(X, n, d, Q, nq, k, self_offset, nbr, len, xn, qn, best, bufp, s);

@@ -64,6 +64,7 @@ constexpr int kOvf = 256;            // shared-memory overflow keys per warp
 constexpr int kVisitLog = 16384;     // ids logged per warp for clearing its bitmap
 constexpr int kGlobalPool = 16384;   // per-warp candidate spill pool entries
 constexpr u64 kMaxKey = ~0ull;
+constexpr int kFeat = 16;
 
 struct SearchArgs {
     const int64_t *row_ptr;
@@ -85,9 +86,11 @@ struct SearchArgs {
     const int32_t *seeds;
     int n_seed;
     int max_exp;
-    int32_t *out_ids;
+    int32_t *out_ids;  // may be NULL (probe only)
     float *out_dist;
     int32_t *stats;
+    float *feat;       // [nq, kFeat] probe features, or NULL
+    float target;      // feature 0 (the recall the prediction is for)
     int *counter;
     unsigned *gbits;  // [slots, bits_words]: visited bitmap past the shared table
     int64_t bits_words;
@@ -283,7 +286,10 @@ template <int V, class T, int HV, int KR> struct Warp {
     int nh, no, ng, cnt, ndc, nexp, nvis, nlog, kk, nscan, es;
     int pf_node, pf_id;  // adjacency row already loaded for the next expansion
     unsigned flags;
-    bool spill, rset, stop, padded;
+    bool spill, rset, stop, padded, capped;
+    int seed_cnt, rins;  // probe features: seeds evaluated, result insertions
+    float seed_sum;
+    u64 seed1, seed2;
     float r2;
     u64 tau;  // every key in the global pool is >= tau (kMaxKey when it is empty)
     double f2, bound2;
@@ -397,13 +403,15 @@ template <int V, class T, int HV, int KR> struct Warp {
 
     // ---------------------------------------------------------------- result list
 
-    __device__ void r_insert(u64 key)
+    // Inserts key into R; false if R keeps its k entries (key would be evicted).
+    __device__ bool r_insert(u64 key)
     {
         const int pos = res.rank(key);
         if (pos >= kk)
-            return;
+            return false;
         res.insert_at(pos, key, lane, kk);
         cnt = min(cnt + 1, kk);
+        return true;
     }
 
     __device__ void update_bound() { bound2 = (rset && !isinf(f2)) ? (double)r2 * f2 : INFINITY; }
@@ -613,6 +621,14 @@ template <int V, class T, int HV, int KR> struct Warp {
         __syncwarp();
         float d2 = distances<Loader<T>>(xs, id, mask);
         u64 key = pack_key(d2, id);
+        if (init && a.feat) {
+            float sd = isnew ? sqrtf(d2) : 0.f;
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1)
+                sd += __shfl_xor_sync(FULL, sd, off);
+            seed_sum += sd;
+            seed_cnt += nnew;
+        }
         if (predict) {
             // next pop = min(S head, nearest batch member if it is pushed)
             const u64 bmin = warp_min_u64(isnew ? key : kMaxKey);
@@ -630,7 +646,8 @@ template <int V, class T, int HV, int KR> struct Warp {
             cm &= cm - 1;
             u64 ck = __shfl_sync(FULL, key, src);
             if (init || !rset || key_d2(ck) <= r2) {
-                r_insert(ck);
+                if (r_insert(ck) && !init)
+                    ++rins;
                 if (!init && cnt == kk) {
                     rset = true;
                     r2 = key_d2(res.get(kk - 1));
@@ -666,7 +683,9 @@ template <int V, class T, int HV, int KR> struct Warp {
         pf_node = -1;
         kk = a.k;
         flags = 0;
-        spill = rset = stop = false;
+        spill = rset = stop = capped = false;
+        seed_cnt = rins = 0;
+        seed_sum = 0.f;
         r2 = INFINITY;
         tau = kMaxKey;
         bound2 = INFINITY;
@@ -680,19 +699,24 @@ template <int V, class T, int HV, int KR> struct Warp {
             }
             batch(id < 0 ? -1 : id, true, false);
         }
+        seed1 = head.get(0);
+        seed2 = head.get(1);
         while (!stop) {
             if (nh == 0) {
                 refill_head();
                 if (nh == 0)
                     break;
             }
+            if (a.max_exp > 0 && nexp >= a.max_exp) {
+                // capped with a candidate still to expand (not merely pending termination)
+                capped = (double)key_d2(__shfl_sync(FULL, head.v[0], 0)) <= bound2;
+                if (capped)
+                    flags |= ONNG_FLAG_LIMIT;
+                break;
+            }
             const u64 sk = pool_pop();
             if ((double)key_d2(sk) > bound2)
                 break;
-            if (a.max_exp > 0 && nexp >= a.max_exp) {
-                flags |= ONNG_FLAG_LIMIT;
-                break;
-            }
             ++nexp;
             const int s = key_id(sk);
             if (predict) {
@@ -747,13 +771,52 @@ template <int V, class T, int HV, int KR> struct Warp {
         }
     }
 
+    // Probe features after the capped search (all logs natural, distances Euclidean).
+    __device__ void features(int64_t q)
+    {
+        const u64 rbk = res.get(0);
+        const u64 rkk = res.get(cnt > 0 ? cnt - 1 : 0);
+        const u64 hk = __shfl_sync(FULL, head.v[0], 0);
+        if (lane != 0)
+            return;
+        const float e6 = 1e-6f;
+        const float ds1 = seed1 == kMaxKey ? 0.f : sqrtf(key_d2(seed1));
+        const float ds2 = seed2 == kMaxKey ? ds1 : sqrtf(key_d2(seed2));
+        const float dmean = seed_cnt > 0 ? seed_sum / (float)seed_cnt : ds1;
+        const float rb = cnt > 0 ? sqrtf(key_d2(rbk)) : ds1;
+        const float rk = cnt > 0 ? sqrtf(key_d2(rkk)) : ds1;
+        const float bound = (rset && !isinf(f2)) ? (float)sqrt(bound2) : INFINITY;
+        float top = capped ? fminf(sqrtf(key_d2(hk)), bound) : bound;
+        if (isinf(top))
+            top = rk;
+        float *f = a.feat + q * kFeat;
+        f[0] = a.target;
+        f[1] = logf(ds1 + e6);
+        f[2] = logf((ds2 + e6) / (ds1 + e6));
+        f[3] = logf((dmean + e6) / (ds1 + e6));
+        f[4] = logf((rb + e6) / (ds1 + e6));
+        f[5] = logf((rk + e6) / (rb + e6));
+        f[6] = logf((top + e6) / (rb + e6));
+        f[7] = (float)ndc / (float)max(1, seed_cnt + nscan);
+        f[8] = (float)nexp / (float)max(1, a.max_exp);
+        f[9] = log1pf((float)ndc);
+        f[10] = (float)rins / (float)max(1, ndc);
+        f[11] = rset ? 1.f : 0.f;
+        f[12] = logf((rk + e6) / (ds1 + e6));
+        f[13] = log1pf((float)nscan);
+        f[14] = capped ? 1.f : 0.f;
+        f[15] = logf((float)a.d) / 8.f;
+    }
+
     __device__ void write(int64_t q)
     {
+        if (a.feat)
+            features(q);
         const int k = a.k_out;
 #pragma unroll
         for (int i = 0; i < KR; ++i) {
             const int e = i * 32 + lane;
-            if (e < k) {
+            if (e < k && a.out_ids) {
                 a.out_ids[q * k + e] = e < cnt ? key_id(res.v[i]) : -1;
                 a.out_dist[q * k + e] = e < cnt ? sqrtf(key_d2(res.v[i])) : INFINITY;
             }
@@ -886,10 +949,10 @@ extern "C" int onng_pad_adjacency(const int64_t *row_ptr, const int32_t *col, in
     return check_launch("onng_pad_adjacency");
 }
 
-extern "C" int onng_search(const onng_index *idx, const float *Q, int64_t nq, const onng_search_params *p,
-                           const int32_t *seeds, int32_t n_seed, const float *eps_q, const int32_t *es_q,
-                           int32_t *out_ids, float *out_dist, int32_t *stats, void *ws, size_t ws_bytes,
-                           onng_stream_t stream)
+static int search_impl(const onng_index *idx, const float *Q, int64_t nq, const onng_search_params *p,
+                       const int32_t *seeds, int32_t n_seed, const float *eps_q, const int32_t *es_q, int32_t *out_ids,
+                       float *out_dist, int32_t *stats, float *feat, float target, void *ws, size_t ws_bytes,
+                       onng_stream_t stream)
 {
     ONNG_REQUIRE(idx && p, ONNG_E_INVAL, "onng_search: NULL index or params");
     ONNG_REQUIRE(nq >= 0 && idx->n > 0 && idx->n <= INT32_MAX, ONNG_E_INVAL, "onng_search: bad sizes");
@@ -910,7 +973,7 @@ extern "C" int onng_search(const onng_index *idx, const float *Q, int64_t nq, co
     }
     if (nq == 0)
         return ONNG_OK;
-    ONNG_REQUIRE(idx->row_ptr && idx->col && idx->X && Q && seeds && out_ids && out_dist, ONNG_E_INVAL,
+    ONNG_REQUIRE(idx->row_ptr && idx->col && idx->X && Q && seeds && (feat || (out_ids && out_dist)), ONNG_E_INVAL,
                  "onng_search: NULL pointer");
     ONNG_REQUIRE(aligned16(idx->X) && aligned16(Q), ONNG_E_INVAL, "onng_search: X and Q must be 16-byte aligned");
     ONNG_REQUIRE(ws, ONNG_E_WORKSPACE, "onng_search: NULL workspace");
@@ -959,6 +1022,8 @@ extern "C" int onng_search(const onng_index *idx, const float *Q, int64_t nq, co
     a.out_ids = out_ids;
     a.out_dist = out_dist;
     a.stats = stats;
+    a.feat = feat;
+    a.target = target;
     cudaStream_t s = to_cuda(stream);
     ONNG_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(int), s), "onng_search: reset counter");
     // the bitmaps start empty; every query leaves its bitmap empty again
@@ -966,4 +1031,23 @@ extern "C" int onng_search(const onng_index *idx, const float *Q, int64_t nq, co
                   "onng_search: clear visited bitmaps");
     L.fn<<<(unsigned)blocks, kWarpsPerCta * 32, L.smem, s>>>(a);
     return check_launch("onng_search");
+}
+
+extern "C" int onng_search(const onng_index *idx, const float *Q, int64_t nq, const onng_search_params *p,
+                           const int32_t *seeds, int32_t n_seed, const float *eps_q, const int32_t *es_q,
+                           int32_t *out_ids, float *out_dist, int32_t *stats, void *ws, size_t ws_bytes,
+                           onng_stream_t stream)
+{
+    return search_impl(idx, Q, nq, p, seeds, n_seed, eps_q, es_q, out_ids, out_dist, stats, nullptr, 0.f, ws,
+                       ws_bytes, stream);
+}
+
+extern "C" int onng_search_probe(const onng_index *idx, const float *Q, int64_t nq, const onng_search_params *p,
+                                 const int32_t *seeds, int32_t n_seed, float target, float *features, int32_t *stats,
+                                 void *ws, size_t ws_bytes, onng_stream_t stream)
+{
+    ONNG_REQUIRE(p && p->max_expansions >= 1, ONNG_E_INVAL, "onng_search_probe: max_expansions must be >= 1");
+    ONNG_REQUIRE(features || nq == 0, ONNG_E_INVAL, "onng_search_probe: NULL features");
+    return search_impl(idx, Q, nq, p, seeds, n_seed, nullptr, nullptr, nullptr, nullptr, stats, features, target, ws,
+                       ws_bytes, stream);
 }

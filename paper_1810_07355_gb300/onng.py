@@ -75,6 +75,14 @@ def load(build_if_missing: bool = True):
                             C.c_int),
             "onng_to_bf16": ([vp, i64, vp, vp], C.c_int),
             "onng_pad_adjacency": ([vp, vp, i64, i32, vp, vp], C.c_int),
+            "onng_search_probe": ([C.POINTER(_Index), vp, i64, C.POINTER(_Params), vp, i32, f32, vp, vp, vp, sz, vp],
+                                  C.c_int),
+            "onng_mlp_nparam": ([], C.c_int),
+            "onng_mlp_forward": ([vp, vp, i64, vp, vp], C.c_int),
+            "onng_mlp_loss_grad": ([vp, vp, vp, i64, vp, vp, vp], C.c_int),
+            "onng_mlp_adam": ([vp, vp, vp, vp, i64, f32, f32, f32, f32, vp], C.c_int),
+            "onng_mlp_train": ([vp, vp, vp, vp, vp, i64, i32, i64, i64, f32, vp, vp, vp], C.c_int),
+            "onng_mlp_predict": ([vp, vp, i64, f32, i32, i32, vp, vp, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -91,7 +99,8 @@ def exported_symbols():
         "onng_adjust_degree_workspace_bytes", "onng_adjust_degree_count", "onng_adjust_degree",
         "onng_adjust_path_workspace_bytes", "onng_adjust_path", "onng_seeds_random",
         "onng_seeds_pivot_workspace_bytes", "onng_seeds_pivot", "onng_search_workspace_bytes", "onng_search",
-        "onng_to_bf16", "onng_pad_adjacency",
+        "onng_to_bf16", "onng_pad_adjacency", "onng_search_probe", "onng_mlp_nparam", "onng_mlp_forward",
+        "onng_mlp_loss_grad", "onng_mlp_adam", "onng_mlp_train", "onng_mlp_predict",
     ]
 
 
@@ -316,3 +325,79 @@ def search(index: Index, Q: torch.Tensor, k: int, e_s: int, eps: float, seeds: t
     _check(lib.onng_search(C.byref(ic), _ptr(Q), nq, C.byref(p), _ptr(seeds), seeds.shape[1], _ptr(eq), _ptr(sq),
                            _ptr(ids), _ptr(dist), _ptr(st), _ptr(ws), ws.numel(), _stream()))
     return ids, dist, st
+
+
+def search_probe(index: Index, Q: torch.Tensor, k: int, e_s: int, eps: float, seeds: torch.Tensor, h: int,
+                 target: float, workspace: SearchWorkspace | None = None):
+    """Algorithm 1 stopped after h expansions: (features float32 [nq,16], stats int32 [nq,4])."""
+    Q = _dev(Q, torch.float32)
+    seeds = _dev(seeds, torch.int32)
+    nq = Q.shape[0]
+    lib = load()
+    p = _Params(k, e_s, float(eps), PREC_FP32, 0, h)
+    ic = index._c()
+    ws = (workspace or _default_ws).get(lib.onng_search_workspace_bytes(nq, C.byref(ic), C.byref(p)), Q.device)
+    feat = torch.empty((nq, 16), dtype=torch.float32, device=Q.device)
+    st = torch.empty((nq, 4), dtype=torch.int32, device=Q.device)
+    _check(lib.onng_search_probe(C.byref(ic), _ptr(Q), nq, C.byref(p), _ptr(seeds), seeds.shape[1], float(target),
+                                 _ptr(feat), _ptr(st), _ptr(ws), ws.numel(), _stream()))
+    return feat, st
+
+
+# ----------------------------------------------------------------------------- predictor network
+
+MLP_NPARAM = 16 * 64 + 64 + 64 * 64 + 64 + 2 * 64 + 2
+
+
+def mlp_init(seed: int = 0, device="cuda") -> torch.Tensor:
+    """He-initialised parameters (flat float32 vector, biases zero)."""
+    g = torch.Generator().manual_seed(seed)
+    parts = []
+    for fan_in, fan_out in ((16, 64), (64, 64), (64, 2)):
+        parts.append(torch.randn(fan_out * fan_in, generator=g) * (2.0 / fan_in) ** 0.5)
+        parts.append(torch.zeros(fan_out))
+    return torch.cat(parts).to(device=device, dtype=torch.float32)
+
+
+def mlp_forward(P: torch.Tensor, X: torch.Tensor) -> torch.Tensor:
+    X = _dev(X, torch.float32)
+    Y = torch.empty((X.shape[0], 2), dtype=torch.float32, device=X.device)
+    _check(load().onng_mlp_forward(_ptr(_dev(P, torch.float32)), _ptr(X), X.shape[0], _ptr(Y), _stream()))
+    return Y
+
+
+def mlp_loss_grad(P: torch.Tensor, X: torch.Tensor, T: torch.Tensor):
+    X = _dev(X, torch.float32)
+    T = _dev(T, torch.float32)
+    G = torch.empty(MLP_NPARAM, dtype=torch.float32, device=X.device)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    _check(load().onng_mlp_loss_grad(_ptr(_dev(P, torch.float32)), _ptr(X), _ptr(T), X.shape[0], _ptr(G), _ptr(loss),
+                                     _stream()))
+    return loss, G
+
+
+def mlp_adam(P, G, M, V, t: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
+    """In-place Adam step on float32 CUDA tensors P, M, V."""
+    _check(load().onng_mlp_adam(_ptr(P), _ptr(G), _ptr(M), _ptr(V), t, lr, beta1, beta2, eps, _stream()))
+
+
+def mlp_train(P, M, V, X, T, steps: int, batch: int, lr: float, t0: int = 0, losses: bool = False):
+    """`steps` Adam steps on consecutive mini-batches, in one kernel; returns the per-step losses if asked."""
+    X = _dev(X, torch.float32)
+    T = _dev(T, torch.float32)
+    G = torch.empty(MLP_NPARAM, dtype=torch.float32, device=X.device)
+    L = torch.empty(max(steps, 1), dtype=torch.float32, device=X.device) if losses else None
+    _check(load().onng_mlp_train(_ptr(P), _ptr(M), _ptr(V), _ptr(X), _ptr(T), X.shape[0], batch, steps, t0, lr,
+                                 _ptr(G), _ptr(L), _stream()))
+    return L
+
+
+def mlp_predict(P, X, alpha: float = 1.0, es_min: int = 1, es_max: int = 32):
+    """bfloat16 evaluation: (eps float32 [B], e_s int32 [B])."""
+    X = _dev(X, torch.float32)
+    B = X.shape[0]
+    eps = torch.empty(B, dtype=torch.float32, device=X.device)
+    es = torch.empty(B, dtype=torch.int32, device=X.device)
+    _check(load().onng_mlp_predict(_ptr(_dev(P, torch.float32)), _ptr(X), B, float(alpha), es_min, es_max, _ptr(eps),
+                                   _ptr(es), _stream()))
+    return eps, es

@@ -67,6 +67,28 @@ def test_knng_tie_heavy_and_duplicates(onng):
     assert_rows_match(host(nbr), host(ln), o_ids, o_len)
 
 
+@pytest.mark.parametrize("d", [64, 128])
+def test_knng_tensor_core_ties(onng, d):
+    """Integer data at d = 64 / 128 goes through the tcgen05 path; heavy ties and
+    duplicate points must still come out in (distance, id) order."""
+    X = synth.small_integers(2000, d, high=3, seed=d)
+    nbr, ln = onng.build_knng(dev(X), 30)
+    o_ids, o_len = oracle.knng(X, 30)
+    assert_rows_match(host(nbr), host(ln), o_ids, o_len)
+
+
+def test_knn_tensor_core_ragged_and_self(onng):
+    """Row and column counts that are not multiples of the 128 x 256 tile, queries
+    that are base rows (self excluded) and queries that are not."""
+    X, Q = synth.workload("sift1m", n=1000 + 77, nq=131)
+    ids, ln = onng.knn(dev(X), dev(X[300:300 + 131]), 17, self_offset=300)
+    o_ids, o_len = oracle.knn(X, X[300:300 + 131], 17, self_ids=np.arange(300, 431))
+    assert_rows_match(host(ids), host(ln), o_ids, o_len)
+    ids, ln = onng.knn(dev(X), dev(Q), 100)
+    o_ids, o_len = oracle.knn(X, Q, 100)
+    assert_rows_match(host(ids), host(ln), o_ids, o_len)
+
+
 def test_knng_float_near_ties_only(onng):
     X, _ = synth.workload("gmm10k", n=2000, nq=1)
     nbr, ln = onng.build_knng(dev(X), 40)

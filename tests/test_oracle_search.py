@@ -211,3 +211,24 @@ def test_adam_matches_torch(oracle_lib):
         tp.grad = torch.from_numpy(G)
         opt.step()
     np.testing.assert_allclose(P, tp.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+def test_probe_features_chain(oracle_lib):
+    """Probe after one hop of the chain trace (Algorithm 1 stopped before the
+    second expansion): node 0 expanded, node 1 visited, R = {1, 0}."""
+    g = json.load(open(os.path.join(GOLDEN, "chain_search.json")))
+    X = np.array(g["X"], np.float32)
+    n = len(X)
+    rows = [[c for c in (i - 1, i + 1) if 0 <= c < n] for i in range(n)]
+    ptr = np.cumsum([0] + [len(r) for r in rows]).astype(np.int64)
+    col = np.array(sum(rows, []), np.int32)
+    Q = np.array([g["query"]], np.float32)
+    f, st = oracle_lib.search_probe(ptr, col, X, Q, 2, 0, 0.0, np.array([g["seeds"]], np.int32), 1, 0.9)
+    e6 = 1e-6
+    want = [0.9, np.log(6.4 + e6), 0.0, 0.0, np.log((5.4 + e6) / (6.4 + e6)), np.log((6.4 + e6) / (5.4 + e6)),
+            0.0, 2 / 2, 1.0, np.log1p(2), 1 / 2, 1.0, 0.0, np.log1p(1), 1.0, np.log(1) / 8]
+    np.testing.assert_allclose(f[0], want, atol=1e-6)
+    assert st[0, 0] == 2 and st[0, 1] == 1
+    # a cap beyond the search length changes nothing: the probe is the full search
+    f, st = oracle_lib.search_probe(ptr, col, X, Q, 2, 0, 0.0, np.array([g["seeds"]], np.int32), 100, 0.9)
+    assert st[0, 1] == 8 and f[0, 14] == 0.0 and abs(f[0, 8] - 0.08) < 1e-12
