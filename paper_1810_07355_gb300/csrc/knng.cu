@@ -397,8 +397,9 @@ template <int KA> struct TcSmem {
     static constexpr int B_ATOM = TC_N * 128;
     static constexpr int A_BYTES = KA * A_ATOM;
     static constexpr int B_STAGE = KA * B_ATOM;
-    // alignment slack, operands, then barriers, TMEM address, flags, thresholds, counts
-    static constexpr int BYTES = 1024 + A_BYTES + TC_STAGES * B_STAGE + 2048;
+    // alignment slack, operands, then barriers, TMEM address, flags, thresholds,
+    // counts and the base norms of two tiles
+    static constexpr int BYTES = 1024 + A_BYTES + TC_STAGES * B_STAGE + 4096;
 };
 
 template <int KC, int KA>
@@ -418,6 +419,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     int *s_ok = reinterpret_cast<int *>(tmem_slot + 1);
     float *s_thr = reinterpret_cast<float *>(s_ok + 4);
     int *s_cnt = reinterpret_cast<int *>(s_thr + TC_M);
+    float *s_xn = reinterpret_cast<float *>(s_cnt + TC_M);  // [2][TC_N], +inf past n
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t row0 = (int64_t)blockIdx.x * TC_M;
@@ -508,13 +510,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else {
         // ------------------------------------------------ epilogue (warps 0-7)
+        // Thread (warp w, lane l) owns query row r = 32 (w % 4) + l and columns
+        // 128 (w / 4) .. +127 of each tile.  The tile's base norms are staged in
+        // shared memory one tile ahead (+inf past n, so no bounds test is needed);
+        // the self column is cleared from a chunk's hit mask, and only hits leave
+        // the fast path.
         const int qd = warp & 3, half = warp >> 2;
         const int r = qd * 32 + lane;
         const int64_t grow = row0 + r;
         const bool row_ok = grow < nq;
         const float qnr = row_ok ? qn[grow] : 0.f;
         const int64_t self = (self_offset >= 0 && row_ok) ? self_offset + grow : -1;
-        float thr = INFINITY;
+        float thr = row_ok ? INFINITY : -INFINITY;
+        s_xn[tid] = tid < n ? xn[tid] : INFINITY;
+        epi_sync();
         for (int64_t t = 0; t < tiles; ++t) {
             const int b = (int)(t & 1);
             if (tid == 0)
@@ -524,24 +533,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 break;
             tc_fence_after();
             const int64_t col0 = t * TC_N + half * 128;
+            const float *xs = s_xn + b * TC_N + half * 128;
+            const int64_t self_local = self - col0;  // in [0, 128) when the self column is here
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 uint32_t v[32];
                 tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * TC_N + half * 128 + c * 32), v);
+                float d2[32];
+                uint32_t hit = 0;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const int64_t col = col0 + c * 32 + j;
-                    if (col < n && row_ok && col != self) {
-                        const float d2 = fmaxf(qnr + __ldg(xn + col) - 2.f * __uint_as_float(v[j]), 0.f);
-                        if (d2 < thr) {
-                            const int pos = atomicAdd(&s_cnt[r], 1);
-                            buf[grow * TC_BUF + pos] = pack_key(d2, (int)col);
-                        }
-                    }
+                    d2[j] = fmaxf(qnr + xs[c * 32 + j] - 2.f * __uint_as_float(v[j]), 0.f);
+                    hit |= (d2[j] < thr ? 1u : 0u) << j;
+                }
+                const int64_t sj = self_local - c * 32;
+                if (sj >= 0 && sj < 32)
+                    hit &= ~(1u << (int)sj);
+                while (hit) {
+                    const int j = __ffs(hit) - 1;
+                    hit &= hit - 1;
+                    float dj = d2[0];
+#pragma unroll
+                    for (int u = 1; u < 32; ++u)
+                        dj = u == j ? d2[u] : dj;
+                    const int pos = atomicAdd(&s_cnt[r], 1);
+                    buf[grow * TC_BUF + pos] = pack_key(dj, (int)(col0 + c * 32 + j));
                 }
             }
             tc_fence_before();
             mbar_arrive(&acce[b]);
+            // stage the next tile's norms into the other half of s_xn
+            {
+                const int64_t nc = (t + 1) * TC_N + tid;
+                s_xn[(b ^ 1) * TC_N + tid] = nc < n ? xn[nc] : INFINITY;
+            }
             epi_sync();
             const bool last = t + 1 == tiles;
             for (int rr = warp; rr < TC_M; rr += TC_EPI / 32) {
@@ -553,7 +578,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     merge_row<KC, TC_BUF>(rr, gr, best, buf, s_thr, s_cnt, lane);
             }
             epi_sync();
-            thr = s_thr[r];
+            if (row_ok)
+                thr = s_thr[r];
         }
     }
     tc_fence_before();
