@@ -192,6 +192,35 @@ int onng_search_probe(const onng_index *idx, const float *Q, int64_t nq, const o
                       const int32_t *seeds, int32_t n_seed, float target, float *features, int32_t *stats,
                       void *ws, size_t ws_bytes, onng_stream_t stream);
 
+/* onng_search without a caller workspace and without any allocation.  The
+ * paper has no counterpart: it is a convenience for callers that cannot
+ * allocate device memory per call, such as a query loop that must not stall
+ * (cudaMalloc and cudaFree may synchronise the whole device), a process whose
+ * device memory is already committed to the index and its batch buffers, or
+ * plain C code with no allocator of its own.
+ *
+ * Arguments, results and errors are those of onng_search; the scratch (query
+ * counter, per-warp visited bitmaps, logs and spill pools) lives in one fixed
+ * array of ONNG_SEARCH_NOALLOC_SCRATCH_BYTES per device, reserved when the
+ * library's search module is loaded and held until the process exits.  One
+ * CTA of the search needs 1 KB + 4 * (n/8 rounded up to 1 KB + 192 KB) of it,
+ * so indexes up to about n = 65 million fit; a larger n returns
+ * ONNG_E_WORKSPACE with the limit in onng_last_error().  Larger query batches
+ * are fine: they run on as many CTAs as the array holds (26 at n = 1M), each
+ * taking queries until none are left.
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current) and keeps it; make that first call before any stream
+ * capture.  Every call clears the parts that must start at zero (the query
+ * counter and the bitmaps) on its stream, so a call sees nothing of the
+ * previous one.  All calls on a device share the one array: calls whose
+ * kernels can overlap on the GPU (other streams, other host threads) race
+ * and give wrong results; order them on one stream or with events. */
+#define ONNG_SEARCH_NOALLOC_SCRATCH_BYTES (32u << 20)
+int onng_search_noalloc(const onng_index *idx, const float *Q, int64_t nq, const onng_search_params *p,
+                        const int32_t *seeds, int32_t n_seed, const float *eps_q, const int32_t *es_q,
+                        int32_t *out_ids, float *out_dist, int32_t *stats, onng_stream_t stream);
+
 /* adj [n, width]: the first `width` entries of every CSR row, -1 past its end */
 int onng_pad_adjacency(const int64_t *row_ptr, const int32_t *col, int64_t n, int32_t width,
                        int32_t *adj, onng_stream_t stream);

@@ -42,6 +42,7 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <mutex>
 #include <type_traits>
 
 #include "common.cuh"
@@ -1050,4 +1051,70 @@ extern "C" int onng_search_probe(const onng_index *idx, const float *Q, int64_t 
     ONNG_REQUIRE(features || nq == 0, ONNG_E_INVAL, "onng_search_probe: NULL features");
     return search_impl(idx, Q, nq, p, seeds, n_seed, nullptr, nullptr, nullptr, nullptr, stats, features, target, ws,
                        ws_bytes, stream);
+}
+
+// ---------------------------------------------------------------------------
+// onng_search without allocation.  Some callers cannot allocate device memory
+// per call: a query loop that must not stall (cudaMalloc and cudaFree may
+// synchronise the whole device), a process whose memory is already committed
+// to the index and its batch buffers, or C code with no allocator of its own.
+// For them the search's scratch lives in one fixed array per device.  The
+// array is reserved when this module is loaded and held until the process
+// exits, so its size is kept modest; search_impl sizes the grid to it.
+//
+// Host code must not hand `g_noalloc_scratch` to a kernel: here that name is a
+// host-side stand-in for the symbol, not its device address.  The address is
+// looked up once per device, with that device current, and then reused.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[ONNG_SEARCH_NOALLOC_SCRATCH_BYTES];
+
+namespace onng {
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+
+int noalloc_scratch(void **out)
+{
+    static std::mutex mu;
+    static void *addr[kNoallocMaxDevices] = {};
+    int dev = -1;
+    ONNG_CUDA_TRY(cudaGetDevice(&dev), "onng_search_noalloc: current device");
+    ONNG_REQUIRE(dev >= 0 && dev < kNoallocMaxDevices, ONNG_E_UNSUPPORTED,
+                 "onng_search_noalloc: device ordinal %d >= %d", dev, kNoallocMaxDevices);
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *ptr = nullptr;
+        ONNG_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_noalloc_scratch), "onng_search_noalloc: scratch address");
+        ONNG_REQUIRE(ptr, ONNG_E_CUDA, "onng_search_noalloc: scratch address is NULL");
+        addr[dev] = ptr;
+    }
+    *out = addr[dev];
+    return ONNG_OK;
+}
+
+}  // namespace
+}  // namespace onng
+
+extern "C" int onng_search_noalloc(const onng_index *idx, const float *Q, int64_t nq, const onng_search_params *p,
+                                   const int32_t *seeds, int32_t n_seed, const float *eps_q, const int32_t *es_q,
+                                   int32_t *out_ids, float *out_dist, int32_t *stats, onng_stream_t stream)
+{
+    ONNG_REQUIRE(idx && p, ONNG_E_INVAL, "onng_search_noalloc: NULL index or params");
+    ONNG_REQUIRE(idx->n > 0 && idx->n <= INT32_MAX, ONNG_E_INVAL, "onng_search_noalloc: bad index size");
+    // one CTA's share: the query counter's slot plus kWarpsPerCta per-warp slots
+    const size_t cap = (size_t)ONNG_SEARCH_NOALLOC_SCRATCH_BYTES;
+    const size_t need = 1024 + (size_t)kWarpsPerCta * slot_bytes(idx->n);
+    ONNG_REQUIRE(need <= cap, ONNG_E_WORKSPACE,
+                 "onng_search_noalloc: an index of n = %lld needs %zu scratch bytes for one CTA, more than the "
+                 "fixed %zu (use onng_search with a caller workspace)",
+                 (long long)idx->n, need, cap);
+    if (nq == 0)
+        return search_impl(idx, Q, nq, p, seeds, n_seed, eps_q, es_q, out_ids, out_dist, stats, nullptr, 0.f,
+                           nullptr, 0, stream);
+    void *ws = nullptr;
+    const int st = noalloc_scratch(&ws);
+    if (st)
+        return st;
+    // search_impl clears the counter and the bitmaps on `stream` before its launch
+    return search_impl(idx, Q, nq, p, seeds, n_seed, eps_q, es_q, out_ids, out_dist, stats, nullptr, 0.f, ws, cap,
+                       stream);
 }

@@ -77,6 +77,8 @@ def load(build_if_missing: bool = True):
             "onng_pad_adjacency": ([vp, vp, i64, i32, vp, vp], C.c_int),
             "onng_search_probe": ([C.POINTER(_Index), vp, i64, C.POINTER(_Params), vp, i32, f32, vp, vp, vp, sz, vp],
                                   C.c_int),
+            "onng_search_noalloc": ([C.POINTER(_Index), vp, i64, C.POINTER(_Params), vp, i32, vp, vp, vp, vp, vp, vp],
+                                    C.c_int),
             "onng_mlp_nparam": ([], C.c_int),
             "onng_mlp_forward": ([vp, vp, i64, vp, vp], C.c_int),
             "onng_mlp_loss_grad": ([vp, vp, vp, i64, vp, vp, vp], C.c_int),
@@ -100,7 +102,7 @@ def exported_symbols():
         "onng_adjust_path_workspace_bytes", "onng_adjust_path", "onng_seeds_random",
         "onng_seeds_pivot_workspace_bytes", "onng_seeds_pivot", "onng_search_workspace_bytes", "onng_search",
         "onng_to_bf16", "onng_pad_adjacency", "onng_search_probe", "onng_mlp_nparam", "onng_mlp_forward",
-        "onng_mlp_loss_grad", "onng_mlp_adam", "onng_mlp_train", "onng_mlp_predict",
+        "onng_mlp_loss_grad", "onng_mlp_adam", "onng_mlp_train", "onng_mlp_predict", "onng_search_noalloc",
     ]
 
 
@@ -324,6 +326,37 @@ def search(index: Index, Q: torch.Tensor, k: int, e_s: int, eps: float, seeds: t
     sq = None if es_q is None else _dev(es_q, torch.int32)
     _check(lib.onng_search(C.byref(ic), _ptr(Q), nq, C.byref(p), _ptr(seeds), seeds.shape[1], _ptr(eq), _ptr(sq),
                            _ptr(ids), _ptr(dist), _ptr(st), _ptr(ws), ws.numel(), _stream()))
+    return ids, dist, st
+
+
+def search_noalloc(index: Index, Q: torch.Tensor, k: int, e_s: int, eps: float, seeds: torch.Tensor,
+                   precision: int = PREC_FP32, k_rerank: int = 0, eps_q: torch.Tensor | None = None,
+                   es_q: torch.Tensor | None = None, max_expansions: int = 0, out=None):
+    """``search`` through onng_search_noalloc: the library allocates nothing and
+    uses its fixed per-device scratch instead of a workspace.
+
+    For callers that cannot allocate device memory per call.  ``out`` =
+    (ids [nq,k] int32, dist [nq,k] float32, stats [nq,4] int32 or None) lets the
+    caller pass the result buffers too; otherwise they are allocated here, by
+    torch, before the call.  Calls that can overlap on the GPU race on the shared
+    scratch; keep them on one stream."""
+    Q = _dev(Q, torch.float32)
+    seeds = _dev(seeds, torch.int32)
+    nq = Q.shape[0]
+    dev = Q.device
+    lib = load()
+    if precision == PREC_BF16:
+        index.with_bf16()
+    p = _Params(k, e_s, float(eps) if math.isfinite(eps) else math.inf, precision, k_rerank, max_expansions)
+    ic = index._c()
+    if out is None:
+        out = (torch.empty((nq, k), dtype=torch.int32, device=dev), torch.empty((nq, k), dtype=torch.float32, device=dev),
+               torch.empty((nq, 4), dtype=torch.int32, device=dev))
+    ids, dist, st = out
+    eq = None if eps_q is None else _dev(eps_q, torch.float32)
+    sq = None if es_q is None else _dev(es_q, torch.int32)
+    _check(lib.onng_search_noalloc(C.byref(ic), _ptr(Q), nq, C.byref(p), _ptr(seeds), seeds.shape[1], _ptr(eq),
+                                   _ptr(sq), _ptr(ids), _ptr(dist), _ptr(st), _stream()))
     return ids, dist, st
 
 
