@@ -51,6 +51,32 @@
 #ifndef ONNG_SEARCH_HV
 #define ONNG_SEARCH_HV 2048
 #endif
+#ifndef ONNG_SEARCH_MAXV
+#define ONNG_SEARCH_MAXV 8  // kernels are built for d <= 128 * ONNG_SEARCH_MAXV (1, 2, 4 or 8)
+#endif
+// Per vector type, for d <= 256 and k <= 32: shared-memory overflow keys per
+// warp (a multiple of 64), the most vectors gathered per round (a power of two)
+// and the resident CTAs per SM the registers are sized for.  Float32 vectors
+// (512 B at d = 128) want 16 gathers in flight per lane; bfloat16 vectors are
+// half the size, so fewer gathers per round and more warps per SM pay more.
+#ifndef ONNG_SEARCH_F32_OVF
+#define ONNG_SEARCH_F32_OVF 256
+#endif
+#ifndef ONNG_SEARCH_F32_GMAX
+#define ONNG_SEARCH_F32_GMAX 16
+#endif
+#ifndef ONNG_SEARCH_F32_MINB
+#define ONNG_SEARCH_F32_MINB 4
+#endif
+#ifndef ONNG_SEARCH_BF16_OVF
+#define ONNG_SEARCH_BF16_OVF 128
+#endif
+#ifndef ONNG_SEARCH_BF16_GMAX
+#define ONNG_SEARCH_BF16_GMAX 8
+#endif
+#ifndef ONNG_SEARCH_BF16_MINB
+#define ONNG_SEARCH_BF16_MINB 6
+#endif
 
 namespace onng {
 namespace {
@@ -61,7 +87,12 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int kWarpsPerCta = 4;
 constexpr int kMaxK = 128;
 constexpr int kMaxSeed = 64;
-constexpr int kOvf = 256;            // shared-memory overflow keys per warp
+template <class T> struct Tune {
+    static constexpr int ovf = ONNG_SEARCH_F32_OVF, gmax = ONNG_SEARCH_F32_GMAX, minb = ONNG_SEARCH_F32_MINB;
+};
+template <> struct Tune<__nv_bfloat16> {
+    static constexpr int ovf = ONNG_SEARCH_BF16_OVF, gmax = ONNG_SEARCH_BF16_GMAX, minb = ONNG_SEARCH_BF16_MINB;
+};
 constexpr int kVisitLog = 16384;     // ids logged per warp for clearing its bitmap
 constexpr int kGlobalPool = 16384;   // per-warp candidate spill pool entries
 constexpr u64 kMaxKey = ~0ull;
@@ -99,9 +130,9 @@ struct SearchArgs {
     u64 *gpool;       // [slots, kGlobalPool]
 };
 
-template <int HV> struct WarpSmem {
+template <int HV, int OVF> struct WarpSmem {
     int vis[HV];
-    u64 ovf[kOvf];
+    u64 ovf[OVF];
 };
 
 __host__ __device__ constexpr int log2i(int v) { return v <= 1 ? 0 : 1 + log2i(v >> 1); }
@@ -272,8 +303,11 @@ template <int G> __device__ __forceinline__ int holder_lane(int g)
 
 template <int V, class T, int HV, int KR> struct Warp {
     // vectors per gather round: 16 loads in flight per lane at d <= 128
-    static constexpr int G = V >= 8 ? 2 : V >= 4 ? 4 : V >= 2 ? 8 : 16;
-    WarpSmem<HV> &sm;
+    static constexpr int G0 = V >= 8 ? 2 : V >= 4 ? 4 : V >= 2 ? 8 : 16;
+    static constexpr int G = G0 < Tune<T>::gmax ? G0 : Tune<T>::gmax;
+    static constexpr int kOvf = Tune<T>::ovf;  // shared-memory overflow keys
+    static_assert(kOvf >= 64 && (kOvf & (kOvf - 1)) == 0, "the overflow holds a power of two >= 64 keys");
+    WarpSmem<HV, kOvf> &sm;
     const SearchArgs &a;
     const void *xs;  // vectors the search reads (float32 or bfloat16)
     int lane;
@@ -295,7 +329,7 @@ template <int V, class T, int HV, int KR> struct Warp {
     u64 tau;  // every key in the global pool is >= tau (kMaxKey when it is empty)
     double f2, bound2;
 
-    __device__ Warp(WarpSmem<HV> &s, const SearchArgs &args, const void *x, int ln, unsigned *gb, int *gl, u64 *gp)
+    __device__ Warp(WarpSmem<HV, kOvf> &s, const SearchArgs &args, const void *x, int ln, unsigned *gb, int *gl, u64 *gp)
         : sm(s), a(args), xs(x), lane(ln), gbits(gb), glog(gl), gpool(gp)
     {
     }
@@ -435,9 +469,10 @@ template <int V, class T, int HV, int KR> struct Warp {
         ng = min(ng + __popc(m), kGlobalPool);
     }
 
-    // Makes room in the full overflow: drops its out-of-bound keys; if all are in
-    // bound, sorts it and moves the farther half to the global pool.
-    __device__ void make_room()
+    // Makes room for `need` (<= 32) more keys in the overflow: drops its
+    // out-of-bound keys; if they still do not fit, sorts it and moves the
+    // farther half to the global pool (so at most kOvf / 2 keys remain).
+    __device__ void make_room(int need)
     {
         int w = 0;
         for (int base = 0; base < no; base += 32) {
@@ -452,13 +487,14 @@ template <int V, class T, int HV, int KR> struct Warp {
             __syncwarp();
         }
         no = w;
-        if (no < kOvf)
+        if (no + need <= kOvf)
             return;
+        // no > kOvf - need >= kOvf / 2, so the element at kOvf / 2 is a real key
         constexpr int N = kOvf / 32;
         u64 v[N];
 #pragma unroll
         for (int i = 0; i < N; ++i)
-            v[i] = sm.ovf[i * 32 + lane];
+            v[i] = i * 32 + lane < no ? sm.ovf[i * 32 + lane] : kMaxKey;
         warp_bitonic_sort<N>(v, lane);
         __syncwarp();
 #pragma unroll
@@ -467,7 +503,7 @@ template <int V, class T, int HV, int KR> struct Warp {
         const u64 first_moved = __shfl_sync(FULL, v[N / 2], 0);
 #pragma unroll
         for (int i = N / 2; i < N; ++i)
-            gpool_append(true, v[i]);
+            gpool_append(v[i] != kMaxKey, v[i]);
         __syncwarp();
         tau = first_moved;
         no = kOvf / 2;
@@ -476,7 +512,7 @@ template <int V, class T, int HV, int KR> struct Warp {
     __device__ void ovf_append(u64 key)
     {
         if (no == kOvf)
-            make_room();
+            make_room(1);
         if (key >= tau) {
             gpool_append(lane == 0, key);
             return;
@@ -561,10 +597,46 @@ template <int V, class T, int HV, int KR> struct Warp {
         __syncwarp();
     }
 
-    // Adds the batch members marked `push` to S (one at a time; typically a few).
+    // Appends the keys of the lanes with `put` (all < tau) to the shared overflow,
+    // making room first if they do not fit; keys that end up >= tau after that
+    // go to the global pool.
+    __device__ void ovf_append_many(bool put, u64 key)
+    {
+        unsigned m = __ballot_sync(FULL, put);
+        if (!m)
+            return;
+        if (no + __popc(m) > kOvf) {
+            make_room(__popc(m));  // tau may drop
+            const bool far = put && key >= tau;
+            gpool_append(far, key);
+            put = put && !far;
+            m = __ballot_sync(FULL, put);
+        }
+        if (put)
+            sm.ovf[no + __popc(m & lanemask_lt(lane))] = key;
+        no += __popc(m);
+        __syncwarp();
+    }
+
+    // Adds the batch members marked `push` to S.  Keys >= tau go to the global
+    // pool and keys >= the head's maximum to the overflow, each in one step;
+    // only keys that enter the sorted head are inserted one at a time.  While S
+    // is the head alone (no overflow, empty pool) every key is inserted in turn.
     __device__ void pool_push(bool push, u64 key)
     {
         unsigned pm = __ballot_sync(FULL, push);
+        if (!pm)
+            return;
+        if (no > 0 || ng > 0) {
+            const bool far = push && key >= tau;
+            gpool_append(far, key);
+            push = push && !far;
+            const u64 hmax = nh > 0 ? __shfl_sync(FULL, head.v[0], nh - 1) : kMaxKey;
+            const bool to_ovf = push && key >= hmax;
+            ovf_append_many(to_ovf, key);
+            push = push && !to_ovf;
+            pm = __ballot_sync(FULL, push);
+        }
         while (pm) {
             const int src = __ffs(pm) - 1;
             pm &= pm - 1;
@@ -831,15 +903,19 @@ template <int V, class T, int HV, int KR> struct Warp {
     }
 };
 
-// Resident CTAs per SM the register budget is sized for (no spills at these
-// counts; shared memory allows 7 CTAs of 4 warps with the 2048-slot table).
-__host__ __device__ constexpr int min_blocks(int V, int KR) { return V <= 2 && KR == 1 ? 4 : 3; }
+// Resident CTAs per SM the register budget is sized for (a few spilled bytes at
+// most).  Shared memory holds 5 CTAs of float32 warps (2048-slot table and 256
+// overflow keys each) or 6 of bfloat16 warps (128 overflow keys).
+template <class T> __host__ __device__ constexpr int min_blocks(int V, int KR)
+{
+    return V <= 2 && KR == 1 ? Tune<T>::minb : 3;
+}
 
 template <int V, class T, int HV, int KR>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, min_blocks(V, KR)) search_kernel(SearchArgs a)
+__global__ void __launch_bounds__(kWarpsPerCta * 32, min_blocks<T>(V, KR)) search_kernel(SearchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto *smem = reinterpret_cast<WarpSmem<HV> *>(smem_raw);
+    auto *smem = reinterpret_cast<WarpSmem<HV, Tune<T>::ovf> *>(smem_raw);
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t slot = (int64_t)blockIdx.x * kWarpsPerCta + warp;
@@ -881,7 +957,7 @@ struct Launch {
 
 template <int V, class T> Launch pick_kr(int k)
 {
-    constexpr size_t sm = sizeof(WarpSmem<ONNG_SEARCH_HV>) * kWarpsPerCta;
+    constexpr size_t sm = sizeof(WarpSmem<ONNG_SEARCH_HV, Tune<T>::ovf>) * kWarpsPerCta;
     if (k <= 32)
         return {search_kernel<V, T, ONNG_SEARCH_HV, 1>, sm};
     return {search_kernel<V, T, ONNG_SEARCH_HV, kMaxK / 32>, sm};
@@ -892,12 +968,15 @@ template <class T> Launch pick_v(int d, int k)
     const int V = (d + 127) / 128;
     if (V <= 1)
         return pick_kr<1, T>(k);
-    if (V <= 2)
-        return pick_kr<2, T>(k);
-    if (V <= 4)
-        return pick_kr<4, T>(k);
-    if (V <= 8)
-        return pick_kr<8, T>(k);
+    if constexpr (ONNG_SEARCH_MAXV >= 2)
+        if (V <= 2)
+            return pick_kr<2, T>(k);
+    if constexpr (ONNG_SEARCH_MAXV >= 4)
+        if (V <= 4)
+            return pick_kr<4, T>(k);
+    if constexpr (ONNG_SEARCH_MAXV >= 8)
+        if (V <= 8)
+            return pick_kr<8, T>(k);
     return {nullptr, 0};
 }
 
@@ -928,7 +1007,11 @@ using namespace onng;
 
 extern "C" size_t onng_search_workspace_bytes(int64_t nq, const onng_index *idx, const onng_search_params *p)
 {
-    Launch L = pick_v<float>(idx ? idx->d : 128, p ? std::max(p->k, p->k_rerank) : 10);
+    // sized for the grid of the kernel that will run (the bfloat16 kernels hold more CTAs per SM)
+    const int d = idx ? idx->d : 128;
+    const bool bf16 = p && p->precision == ONNG_PREC_BF16;
+    const int kr = p ? (bf16 ? std::max(p->k, p->k_rerank) : p->k) : 10;
+    Launch L = bf16 ? pick_v<__nv_bfloat16>(d, kr) : pick_v<float>(d, kr);
     int per_sm = 16;
     if (!L.fn || resident_blocks(L, &per_sm) != ONNG_OK)
         per_sm = 16;

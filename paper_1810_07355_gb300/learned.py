@@ -145,6 +145,53 @@ def learned_search(pred: Predictor, index, Q, k, seeds, target, alpha=1.0, preci
     return ids, dist, st, eps_q, es_q
 
 
+_OW3, _OB3 = 16 * 64 + 64 + 64 * 64 + 64, 16 * 64 + 64 + 64 * 64 + 64 + 2 * 64
+
+
+def shrink(pred: Predictor, beta: float, ybar: float, es_fixed: int | None = None) -> Predictor:
+    """The network with its eps output pulled toward the constant ybar:
+    y0' = ybar + beta (y0 - ybar), folded into the last layer (W3[0] *= beta,
+    b3[0] = beta b3[0] + (1 - beta) ybar).  beta = 0 is one eps for every query
+    (the fixed policy, scaled by alpha); beta = 1 is the network as trained.
+    es_fixed, if given, pins e_s for every query."""
+    P = pred.P.clone()
+    P[_OW3:_OW3 + 64] *= beta
+    P[_OB3] = beta * P[_OB3] + (1.0 - beta) * ybar
+    lo, hi = (es_fixed, es_fixed) if es_fixed is not None else (pred.es_min, pred.es_max)
+    return Predictor(P, h=pred.h, probe_es=pred.probe_es, probe_eps=pred.probe_eps, es_min=lo, es_max=hi,
+                     losses=pred.losses)
+
+
+def select_shrinkage(pred, index, Q, gt, seeds, k, target_recall, t, betas=(0.0, 0.25, 0.5, 0.75, 1.0),
+                     es_options=(None,), **kw):
+    """On a held-out query set, for each (beta, e_s option): calibrate alpha to the
+    target mean recall and count distance computations per query, of the search
+    and of the probe.  Rows that miss the target (alpha at its upper bound) are
+    kept in the table but never chosen.  beta = 0 without the probe is the fixed
+    policy (one eps for all queries); it is the row {"beta": None}.
+
+    Returns (best row, ybar, table); best["beta"] is None when the fixed policy
+    is cheapest."""
+    feat, _ = onng.search_probe(index, Q, k, pred.probe_es, pred.probe_eps, seeds, pred.h, t)
+    ybar = float(onng.mlp_forward(pred.P, feat)[:, 0].mean())
+    table = []
+    for es_fixed in es_options:
+        for beta in betas:
+            pb = shrink(pred, beta, ybar, es_fixed)
+            alpha = calibrate_alpha(pb, index, Q, gt, seeds, k, target_recall, t, **kw)
+            ids, _, st, _, _ = learned_search(pb, index, Q, k, seeds, t, alpha, **kw)
+            _, pst = onng.search_probe(index, Q, k, pb.probe_es, pb.probe_eps, seeds, pb.h, t)
+            row = {"beta": beta, "es_fixed": es_fixed, "alpha": alpha, "recall": float(recall_per_query(ids, gt).mean()),
+                   "dc_search": float(st[:, 0].float().mean()), "dc_probe": float(pst[:, 0].float().mean())}
+            row["dc"] = row["dc_search"] + row["dc_probe"]
+            table.append(row)
+            if beta == 0.0 and es_fixed is not None:
+                table.append(dict(row, beta=None, dc_probe=0.0, dc=row["dc_search"]))
+    ok = [r for r in table if r["recall"] >= target_recall - 1e-9]
+    best = min(ok, key=lambda r: r["dc"]) if ok else None
+    return best, ybar, table
+
+
 def calibrate_lambda(pred, index, Q, gt, seeds, k, target_recall, lo=-7.0, hi=-2.0, iters=12, **kw):
     """Largest price lambda (bisection on log10 lambda) whose mean recall@k reaches
     target_recall; returns the feature value log10(lambda)."""

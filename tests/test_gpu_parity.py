@@ -197,6 +197,16 @@ def test_seeds_pivot_integer_exact(onng):
     assert np.array_equal(host(s), oracle.seeds_pivot(X[:50], Q, 1024, 64))
 
 
+@pytest.mark.parametrize("d,P,nq,n_seed", [(260, 200, 37, 12), (8, 64, 16, 64), (128, 2048, 5, 1)])
+def test_seeds_pivot_tiles_and_ragged_edges(onng, d, P, nq, n_seed):
+    """Several coordinate chunks, a ragged last pivot tile and query group, and
+    many equal distances (small integers): ids equal the oracle's, ties by pivot index."""
+    X = synth.small_integers(3000, d, high=4, seed=d)
+    Q = synth.small_integers(nq, d, high=4, seed=d + 1)
+    s = onng.seeds_pivot(dev(X), dev(Q), P, n_seed)
+    assert np.array_equal(host(s), oracle.seeds_pivot(X, Q, P, n_seed))
+
+
 # ----------------------------------------------------------------------------- search
 
 @pytest.fixture(scope="module")
