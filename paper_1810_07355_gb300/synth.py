@@ -147,3 +147,27 @@ def workload(name: str, n: int | None = None, nq: int | None = None, train: int 
     if train:
         return base, queries, w["gen"](train, seed=b + 200, **kw)
     return base, queries
+
+
+def request_trace(seconds: float, rate_qps: float, seed: int = SEED_BASE + 5, max_size: int = 256,
+                  ks=(1, 10, 100), recalls=(0.9, 0.95, 0.99)):
+    """Seeded request trace for the serving loop: Poisson arrivals whose mean
+    query rate is ``rate_qps``; request sizes L = floor(exp(U[0, ln(max_size+1))))
+    clipped to [1, max_size] (log-uniform, mean ~46 at 256); k and the required
+    recall uniform over ``ks`` / ``recalls``.
+
+    Returns a structured array (arrival seconds, first query row, size, k, recall)
+    sorted by arrival; the rows index a query matrix of ``sum(size)`` rows."""
+    rng = _rng(seed)
+    lo, hi = 0.0, float(np.log(max_size + 1))
+    mean_size = float(np.mean(np.clip(np.floor(np.exp(rng.uniform(lo, hi, 200_000))), 1, max_size)))
+    req_rate = rate_qps / mean_size
+    count = int(rng.poisson(req_rate * seconds))
+    arrival = np.sort(rng.uniform(0.0, seconds, count))
+    size = np.clip(np.floor(np.exp(rng.uniform(lo, hi, count))), 1, max_size).astype(np.int64)
+    first = np.concatenate([[0], np.cumsum(size)[:-1]]).astype(np.int64)
+    k = np.asarray(ks, dtype=np.int64)[rng.integers(0, len(ks), count)]
+    rec = np.asarray(recalls, dtype=np.float64)[rng.integers(0, len(recalls), count)]
+    out = np.zeros(count, dtype=[("arrival", "f8"), ("first", "i8"), ("size", "i8"), ("k", "i8"), ("recall", "f8")])
+    out["arrival"], out["first"], out["size"], out["k"], out["recall"] = arrival, first, size, k, rec
+    return out
