@@ -72,6 +72,12 @@ def _load():
             lib.oracle_search_probe.restype = i32
             lib.oracle_bf16_round.argtypes = [vp, i64, vp]
             lib.oracle_bf16_round.restype = None
+            lib.oracle_e4m3_encode.argtypes = [vp, i64, vp]
+            lib.oracle_e4m3_encode.restype = None
+            lib.oracle_e4m3_decode.argtypes = [vp, i64, vp]
+            lib.oracle_e4m3_decode.restype = None
+            lib.oracle_fp8_quantize.argtypes = [vp, i64, i32, vp, vp, vp]
+            lib.oracle_fp8_quantize.restype = None
             lib.oracle_mlp_nparam.restype = i32
             lib.oracle_mlp_forward.argtypes = [vp, vp, i64, vp]
             lib.oracle_mlp_forward.restype = None
@@ -245,6 +251,34 @@ def search_probe(ptr, col, X, Q, k: int, e_s: int, eps: float, seeds, h: int, ta
                                      seeds.shape[1], h, float(target), _p(feat), _p(stats), threads)
     assert rc == 0, rc
     return feat, stats
+
+
+def e4m3_encode(x):
+    """FP8 e4m3 codes (uint8): nearest finite value, ties to even, saturating at 448."""
+    x = _c(x, np.float32)
+    y = np.empty(x.shape, dtype=np.uint8)
+    _load().oracle_e4m3_encode(_p(x), x.size, _p(y))
+    return y
+
+
+def e4m3_decode(codes):
+    """float32 values of FP8 e4m3 codes."""
+    c = _c(codes, np.uint8)
+    y = np.empty(c.shape, dtype=np.float32)
+    _load().oracle_e4m3_decode(_p(c), c.size, _p(y))
+    return y
+
+
+def fp8_quantize(X):
+    """(scale float32 [d], codes uint8 [n, d], dequantised float32 [n, d]) with
+    c_j = max_i |x_ij| / 448 and code = e4m3(x_ij / c_j)."""
+    X = _c(X, np.float32)
+    n, d = X.shape
+    scale = np.empty(d, dtype=np.float32)
+    codes = np.empty((n, d), dtype=np.uint8)
+    xq = np.empty((n, d), dtype=np.float32)
+    _load().oracle_fp8_quantize(_p(X), n, d, _p(scale), _p(codes), _p(xq))
+    return scale, codes, xq
 
 
 def bf16_round(x):

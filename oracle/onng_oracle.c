@@ -26,6 +26,8 @@
  *   oracle_seeds_pivot    nearest-pivot seed rule (stands in for the vp-tree
  *                         seeds of Sec. 2 / Table 5, which the paper leaves unspecified)
  *   oracle_bf16_round     bfloat16 round-to-nearest-even of float32 inputs
+ *   oracle_fp8_quantize   FP8 e4m3 codes with per-dimension scales (and the
+ *                         e4m3 encode / decode it rests on)
  *   oracle_mlp_*          the per-query (eps, e_s) predictor network (no paper
  *                         counterpart; the paper's fixed policy is Eq. 1)
  */
@@ -833,6 +835,87 @@ void oracle_bf16_round(const float *x, int64_t m, float *y)
 {
     for (int64_t t = 0; t < m; ++t)
         y[t] = bf16_round1(x[t]);
+}
+
+/*
+ * FP8 e4m3 with per-dimension scales (a spec precision form; the paper is
+ * silent).  e4m3 here is the finite variant: 1 sign, 4 exponent (bias 7) and 3
+ * mantissa bits, no infinities, 0x7F / 0xFF are NaN, largest finite 448;
+ * subnormals are m * 2^-9.  Reading for the scales: c_j = max_i |x_ij| / 448 in
+ * float32 (1 for an all-zero column), so every scaled coordinate x_ij / c_j
+ * (float32 division) lies in [-448, 448] up to one rounding.  The code of a value
+ * is its nearest e4m3 value, ties to the even code, magnitudes above 448 stored
+ * as 448 (saturation).  The dequantised coordinate is the float32 product
+ * c_j * e4m3(code).
+ */
+static float e4m3_decode1(uint8_t code)
+{
+    const int e = (code >> 3) & 15, m = code & 7;
+    float v;
+    if ((code & 0x7F) == 0x7F)
+        return NAN;
+    if (e == 0)
+        v = (float)m * ldexpf(1.0f, -9);
+    else
+        v = (1.0f + (float)m / 8.0f) * ldexpf(1.0f, e - 7);
+    return (code & 0x80) ? -v : v;
+}
+
+static uint8_t e4m3_encode1(float x)
+{
+    if (isnan(x))
+        return 0x7F;
+    const uint8_t sign = signbit(x) ? 0x80 : 0;
+    const float a = fabsf(x);
+    /* codes 0 .. 0x7E hold the non-negative finite values in increasing order:
+       the nearest one by binary search, ties to the even code */
+    int lo = 0, hi = 0x7E;
+    if (a >= e4m3_decode1(0x7E))
+        return sign | 0x7E;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (e4m3_decode1((uint8_t)mid) <= a)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    const double dl = (double)a - (double)e4m3_decode1((uint8_t)lo);
+    const double dh = (double)e4m3_decode1((uint8_t)hi) - (double)a;
+    int c = dl < dh ? lo : dh < dl ? hi : ((lo & 1) ? hi : lo);
+    return sign | (uint8_t)c;
+}
+
+void oracle_e4m3_decode(const uint8_t *codes, int64_t m, float *out)
+{
+    for (int64_t t = 0; t < m; ++t)
+        out[t] = e4m3_decode1(codes[t]);
+}
+
+void oracle_e4m3_encode(const float *x, int64_t m, uint8_t *codes)
+{
+    for (int64_t t = 0; t < m; ++t)
+        codes[t] = e4m3_encode1(x[t]);
+}
+
+/* scale [d], codes [n, d] and the dequantised vectors xq [n, d] (may be NULL) */
+void oracle_fp8_quantize(const float *X, int64_t n, int d, float *scale, uint8_t *codes, float *xq)
+{
+    for (int j = 0; j < d; ++j) {
+        float mx = 0.0f;
+        for (int64_t i = 0; i < n; ++i) {
+            const float a = fabsf(X[i * d + j]);
+            mx = a > mx ? a : mx;
+        }
+        scale[j] = mx > 0.0f ? mx / 448.0f : 1.0f;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int j = 0; j < d; ++j) {
+            const float v = X[i * d + j] / scale[j];
+            const uint8_t c = e4m3_encode1(v);
+            codes[i * d + j] = c;
+            if (xq)
+                xq[i * d + j] = scale[j] * e4m3_decode1(c);
+        }
 }
 
 /* ------------------------------------------------------------- MLP (O6) */

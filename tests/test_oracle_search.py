@@ -232,3 +232,47 @@ def test_probe_features_chain(oracle_lib):
     # a cap beyond the search length changes nothing: the probe is the full search
     f, st = oracle_lib.search_probe(ptr, col, X, Q, 2, 0, 0.0, np.array([g["seeds"]], np.int32), 100, 0.9)
     assert st[0, 1] == 8 and f[0, 14] == 0.0 and abs(f[0, 8] - 0.08) < 1e-12
+
+
+def test_e4m3_matches_torch_float8(oracle_lib):
+    """The oracle's e4m3 encode / decode against torch's float8_e4m3fn (round to
+    nearest even) on random values, every midpoint between neighbouring codes,
+    and all 256 codes."""
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("torch without float8_e4m3fn")
+    rng = np.random.default_rng(5)
+    codes = np.arange(256, dtype=np.uint8)
+    want = torch.from_numpy(codes).view(torch.float8_e4m3fn).float().numpy()
+    got = oracle_lib.e4m3_decode(codes)
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    assert np.array_equal(got[~np.isnan(got)], want[~np.isnan(want)])
+    pos = np.sort(got[:0x7F])
+    mids = ((pos[1:].astype(np.float64) + pos[:-1]) / 2).astype(np.float32)
+    x = np.concatenate([rng.uniform(-448, 448, 50_000), rng.uniform(-1, 1, 50_000), rng.uniform(-0.02, 0.02, 20_000),
+                        mids, -mids, pos, [0.0, -0.0, 448.0, -448.0]]).astype(np.float32)
+    want = torch.from_numpy(x).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    assert np.array_equal(oracle_lib.e4m3_encode(x), want)
+    # saturation (torch gives NaN there): the largest finite code
+    big = np.array([449.0, 464.0, 1e6, 3e38, -500.0], dtype=np.float32)
+    assert np.array_equal(oracle_lib.e4m3_encode(big), [0x7E, 0x7E, 0x7E, 0x7E, 0xFE])
+
+
+def test_fp8_quantize_scales_and_error_bound(oracle_lib):
+    """c_j = max |x_ij| / 448 (1 for a zero column); every dequantised value is
+    within half a step of e4m3 (2^-4 relative, 2^-10 c_j absolute near zero)."""
+    rng = np.random.default_rng(6)
+    X = rng.normal(0, 3, size=(500, 24)).astype(np.float32)
+    X[:, 5] = 0.0
+    X[:, 7] = np.abs(X[:, 7]) * 1e-4
+    scale, codes, xq = oracle_lib.fp8_quantize(X)
+    mx = np.abs(X).max(0)
+    assert np.array_equal(scale, np.where(mx > 0, mx / np.float32(448.0), np.float32(1.0)).astype(np.float32))
+    assert np.array_equal(xq, (scale[None, :] * oracle_lib.e4m3_decode(codes)).astype(np.float32))
+    err = np.abs(xq.astype(np.float64) - X)
+    bound = np.maximum(np.abs(X) * 2.0 ** -4, scale[None, :] * 2.0 ** -10) * (1 + 1e-6)
+    assert np.all(err <= bound)
+    assert np.all(xq[:, 5] == 0.0)
+    # the column maximum is stored exactly (it scales to 448, a code)
+    j = np.abs(X).argmax(0)
+    assert np.allclose(np.abs(xq[j, np.arange(24)]), mx, rtol=1e-6)
