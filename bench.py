@@ -10,6 +10,7 @@ already resident in HBM.  Three forms are timed, each at the operating point
 where mean recall@10 against exact ground truth is >= 0.95:
   fp32     plain search, one global eps (bisection), fixed e_s
   bf16     the same with bfloat16 vectors and a float32 rerank of k_rerank
+  fp8      the same with FP8 e4m3 vectors (per-dimension scales) and the rerank
   learned  bf16 search with per-query (eps, e_s) from the predictor network:
            probe (first h hops) -> bfloat16 network -> search.  The network is
            trained on the GPU on labels of 15,000 training queries; on 5,000
@@ -67,7 +68,7 @@ def parse():
     ap.add_argument("--target", type=float, default=0.95)
     ap.add_argument("--k-rerank", type=int, default=20)
     ap.add_argument("--probe-hops", type=int, default=4)
-    ap.add_argument("--forms", default="fp32,bf16,learned",
+    ap.add_argument("--forms", default="fp32,bf16,fp8,learned",
                     help="forms to time (comma list of fp32, bf16, learned); the value is the last one")
     ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--eps-fp32", type=float, default=None, help="use this eps instead of calibrating")
@@ -211,6 +212,9 @@ def main():
     def run16(eps):
         return onng.search(idx, Qd, a.k, a.e_s, eps, seeds, precision=onng.PREC_BF16, k_rerank=a.k_rerank)
 
+    def run8(eps):
+        return onng.search(idx, Qd, a.k, a.e_s, eps, seeds, precision=onng.PREC_FP8, k_rerank=a.k_rerank)
+
     eps32 = a.eps_fp32 if a.eps_fp32 is not None else calibrate(run32, gt, a.target)
     config = {"workload": f"sift-like n={a.n} d=128 int0-255 fp32, {a.nq} queries, top-{a.k}",
               "knng_k": a.knn_k, "e_o": a.e_o, "e_i": a.e_i, "e_s": a.e_s,
@@ -224,6 +228,10 @@ def main():
     eps16 = a.eps_bf16 if a.eps_bf16 is not None else calibrate(run16, gt, a.target)
     config["eps_bf16"] = round(eps16, 5)
     forms = tuple(f for f in a.forms.split(",") if f)
+    eps8 = None
+    if "fp8" in forms:
+        eps8 = calibrate(run8, gt, a.target)
+        config["eps_fp8"] = round(eps8, 5)
     pred, t_pred, alpha = None, 1.0, 1.0
     if "learned" in forms:
         # the learned form (all untimed preparation): labels from plain-search sweeps of
@@ -279,6 +287,8 @@ def main():
         e.record(stream)
         if form == "fp32":
             ids, _, st = onng.search(idx, Qd, a.k, a.e_s, eps32, s)
+        elif form == "fp8":
+            ids, _, st = onng.search(idx, Qd, a.k, a.e_s, eps8, s, precision=onng.PREC_FP8, k_rerank=a.k_rerank)
         else:
             ids, _, st = onng.search(idx, Qd, a.k, a.e_s, eps16, s, precision=onng.PREC_BF16, k_rerank=a.k_rerank)
         return ids, st, e
@@ -328,7 +338,7 @@ def main():
     kern = {f: float(np.mean(res[f][1])) / 1e3 for f in forms}
     byt, ndc = {}, {}
     for f in forms:
-        byt[f], ndc[f] = search_bytes(res[f][2][1], d, a, 4 if f == "fp32" else 2, f != "fp32")
+        byt[f], ndc[f] = search_bytes(res[f][2][1], d, a, {"fp32": 4, "fp8": 1}.get(f, 2), f != "fp32")
     head = forms[-1]
     if head == "learned" and config["learned"]["fixed_policy_cheaper_on_select_queries"] and "bf16" in forms:
         head = "bf16"
@@ -342,7 +352,7 @@ def main():
         per_dc = tr.get("dram_bytes_per_dc", {}).get(kform)
         if tr.get("search_src_sha256") == hashlib.sha256(src).hexdigest() and per_dc:
             traffic = round(per_dc * ndc[head] * a.nq)
-    names = {"fp32": "plain fp32", "bf16": "fixed-eps bf16 + fp32 rerank",
+    names = {"fp32": "plain fp32", "bf16": "fixed-eps bf16 + fp32 rerank", "fp8": "fixed-eps fp8 e4m3 + fp32 rerank",
              "learned": "learned per-query eps/e_s, bf16 + fp32 rerank"}
     roof = {"bound": "hbm", "achieved": round(byt[head] / kern[head] / 1e9, 1), "peak": peak, "unit": "GB/s",
             "frac": round(byt[head] / kern[head] / 1e9 / peak, 4), "traffic": traffic,
@@ -355,7 +365,7 @@ def main():
 
     e2e = end_to_end(onng, torch, a, idx, Q, head, pred, t_pred, alpha, eps32 if head == "fp32" else eps16, dev)
     cpu = cpu_baseline(a, idx, X, Q, seeds, eps32) if rank == 0 and world == 1 else None
-    per_step = {"fp32": 2, "bf16": 2, "learned": 4}
+    per_step = {"fp32": 2, "bf16": 2, "fp8": 2, "learned": 4}
     if rank == 0:
         line = {"metric": METRIC, "value": round(qps[head], 1), "unit": "queries/s", "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms[head], 4),

@@ -136,8 +136,11 @@ int onng_seeds_pivot(const float *X, int64_t n, int32_t d, const float *Q, int64
  * float32 [n, d].  Optional: adj [n, adj_width] int32, each row's first
  * adj_width entries padded with -1 (onng_pad_adjacency), used instead of the
  * CSR lists whenever e_s <= adj_width; X_bf16 [n, d] (bfloat16 bits), used when
- * precision == ONNG_PREC_BF16, in which case the final list of k_rerank >= k
- * candidates is rescored in float32 against X and the best k are returned.
+ * precision == ONNG_PREC_BF16; X_fp8 [n, d] e4m3 codes with fp8_scale [d]
+ * (onng_to_fp8), used when precision == ONNG_PREC_FP8 (distances on the float32
+ * products scale_j * e4m3).  In both reduced forms the final list of
+ * k_rerank >= k candidates is rescored in float32 against X and the best k are
+ * returned.
  *
  * Outputs: out_ids [nq, k] int32 and out_dist [nq, k] float32 (Euclidean), sorted
  * by (distance, id), padded -1 / +inf; stats [nq, 4] int32 (optional):
@@ -148,7 +151,7 @@ int onng_seeds_pivot(const float *X, int64_t n, int32_t d, const float *Q, int64
  * a spill pool for candidates beyond the register pool; it grows with n, and a
  * smaller workspace than the query runs fewer warps.
  */
-enum onng_precision { ONNG_PREC_FP32 = 0, ONNG_PREC_BF16 = 1 };
+enum onng_precision { ONNG_PREC_FP32 = 0, ONNG_PREC_BF16 = 1, ONNG_PREC_FP8 = 2 };
 
 typedef struct {
     const int64_t *row_ptr;
@@ -159,6 +162,8 @@ typedef struct {
     int64_t n;
     int32_t d;
     int32_t adj_width;
+    const uint8_t *X_fp8;    /* ONNG_PREC_FP8: e4m3 codes [n, d] from onng_to_fp8 */
+    const float *fp8_scale;  /* ONNG_PREC_FP8: per-dimension scales [d] */
 } onng_index;
 
 typedef struct {
@@ -255,6 +260,13 @@ int onng_mlp_train(float *P, float *M, float *V, const float *X, const float *T,
                    int64_t steps, int64_t t0, float lr, float *G, float *losses, onng_stream_t stream);
 int onng_mlp_predict(const float *P, const float *X, int64_t B, float alpha, int32_t es_min,
                      int32_t es_max, float *eps_out, int32_t *es_out, onng_stream_t stream);
+
+/* FP8 e4m3 copy of a vector set X [n, d] for the FP8 search form (no paper
+ * counterpart): scale [d] = max_i |x_ij| / 448 in float32 (1 for an all-zero
+ * column) and out [n, d] = e4m3(x_ij / scale_j), the nearest finite e4m3 value
+ * with ties to even, saturating at 448.  The search dequantises a coordinate as
+ * the float32 product scale_j * e4m3(code).  X must be finite. */
+int onng_to_fp8(const float *X, int64_t n, int32_t d, float *scale, uint8_t *out, onng_stream_t stream);
 
 /* float32 -> bfloat16 (round to nearest even) copy of a vector set, for X_bf16 */
 int onng_to_bf16(const float *X, int64_t count, uint16_t *out, onng_stream_t stream);

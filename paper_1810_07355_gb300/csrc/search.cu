@@ -38,6 +38,7 @@
 // double: d^2 <= r^2 (1 + eps)^2.  For integer-valued inputs with squared
 // distances below 2^24 every decision then equals the float64 algorithm's.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <climits>
@@ -77,6 +78,15 @@
 #ifndef ONNG_SEARCH_BF16_MINB
 #define ONNG_SEARCH_BF16_MINB 6
 #endif
+#ifndef ONNG_SEARCH_FP8_OVF
+#define ONNG_SEARCH_FP8_OVF 128
+#endif
+#ifndef ONNG_SEARCH_FP8_GMAX
+#define ONNG_SEARCH_FP8_GMAX 8
+#endif
+#ifndef ONNG_SEARCH_FP8_MINB
+#define ONNG_SEARCH_FP8_MINB 6
+#endif
 
 namespace onng {
 namespace {
@@ -93,6 +103,9 @@ template <class T> struct Tune {
 template <> struct Tune<__nv_bfloat16> {
     static constexpr int ovf = ONNG_SEARCH_BF16_OVF, gmax = ONNG_SEARCH_BF16_GMAX, minb = ONNG_SEARCH_BF16_MINB;
 };
+template <> struct Tune<__nv_fp8_e4m3> {
+    static constexpr int ovf = ONNG_SEARCH_FP8_OVF, gmax = ONNG_SEARCH_FP8_GMAX, minb = ONNG_SEARCH_FP8_MINB;
+};
 constexpr int kVisitLog = 16384;     // ids logged per warp for clearing its bitmap
 constexpr int kGlobalPool = 16384;   // per-warp candidate spill pool entries
 constexpr u64 kMaxKey = ~0ull;
@@ -105,6 +118,8 @@ struct SearchArgs {
     int adj_w;
     const float *X;
     const uint16_t *Xb;
+    const uint8_t *X8;     // e4m3 codes, dequantised as scale8[j] * e4m3
+    const float *scale8;
     int64_t n;
     int d;
     const float *Q;
@@ -241,6 +256,18 @@ template <> struct Loader<__nv_bfloat16> {
         return f;
     }
 };
+// e4m3 codes, 4 per 32-bit load; the per-dimension scale is applied by the caller
+template <> struct Loader<__nv_fp8_e4m3> {
+    static __device__ __forceinline__ float4 load(const void *base, int64_t id, int d, int c)
+    {
+        const unsigned *p = reinterpret_cast<const unsigned *>(static_cast<const uint8_t *>(base) + id * d) + c;
+        const unsigned u = __ldg(p);
+        const __half2 lo(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u & 0xFFFFu), __NV_E4M3));
+        const __half2 hi(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u >> 16), __NV_E4M3));
+        const float2 a = __half22float2(lo), b = __half22float2(hi);
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+};
 
 __device__ __forceinline__ float sqdiff4(float4 a, float4 b, float acc)
 {
@@ -315,6 +342,7 @@ template <int V, class T, int HV, int KR> struct Warp {
     int *glog;
     u64 *gpool;
     float4 qv[V];
+    float4 sv[V];  // e4m3 form: the per-dimension scales of this lane's coordinates
     RegList<1> head;  // the nearest candidates, sorted
     RegList<KR> res;
     // per-query state, uniform across the warp
@@ -413,6 +441,11 @@ template <int V, class T, int HV, int KR> struct Warp {
                 for (int v = 0; v < V; ++v) {
                     const int c = lane + 32 * v;
                     xv[g][v] = L::load(base, gid[g], a.d, c < chunks ? c : 0);
+                    if constexpr (std::is_same<L, Loader<__nv_fp8_e4m3>>::value) {
+                        // dequantise with a rounded product (never fused into the difference)
+                        xv[g][v] = make_float4(__fmul_rn(sv[v].x, xv[g][v].x), __fmul_rn(sv[v].y, xv[g][v].y),
+                                               __fmul_rn(sv[v].z, xv[g][v].z), __fmul_rn(sv[v].w, xv[g][v].w));
+                    }
                 }
             float acc[G];
 #pragma unroll
@@ -740,6 +773,9 @@ template <int V, class T, int HV, int KR> struct Warp {
         for (int v = 0; v < V; ++v) {
             int c = lane + 32 * v;
             qv[v] = c < (d >> 2) ? __ldg(reinterpret_cast<const float4 *>(qp) + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (std::is_same<T, __nv_fp8_e4m3>::value)
+                sv[v] = c < (d >> 2) ? __ldg(reinterpret_cast<const float4 *>(a.scale8) + c)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         const float eps = a.eps_q ? a.eps_q[q] : a.eps;
         es = a.es_q ? a.es_q[q] : a.e_s;
@@ -919,7 +955,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, min_blocks<T>(V, KR)) searc
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t slot = (int64_t)blockIdx.x * kWarpsPerCta + warp;
-    const void *xs = std::is_same<T, float>::value ? static_cast<const void *>(a.X) : static_cast<const void *>(a.Xb);
+    const void *xs = std::is_same<T, float>::value           ? static_cast<const void *>(a.X)
+                     : std::is_same<T, __nv_bfloat16>::value ? static_cast<const void *>(a.Xb)
+                                                              : static_cast<const void *>(a.X8);
     Warp<V, T, HV, KR> w(smem[warp], a, xs, lane, a.gbits + slot * a.bits_words, a.glog + slot * kVisitLog,
                          a.gpool + slot * kGlobalPool);
     for (;;) {
@@ -1007,11 +1045,13 @@ using namespace onng;
 
 extern "C" size_t onng_search_workspace_bytes(int64_t nq, const onng_index *idx, const onng_search_params *p)
 {
-    // sized for the grid of the kernel that will run (the bfloat16 kernels hold more CTAs per SM)
+    // sized for the grid of the kernel that will run (the reduced-precision kernels hold more CTAs per SM)
     const int d = idx ? idx->d : 128;
-    const bool bf16 = p && p->precision == ONNG_PREC_BF16;
-    const int kr = p ? (bf16 ? std::max(p->k, p->k_rerank) : p->k) : 10;
-    Launch L = bf16 ? pick_v<__nv_bfloat16>(d, kr) : pick_v<float>(d, kr);
+    const int prec = p ? p->precision : ONNG_PREC_FP32;
+    const int kr = p ? (prec != ONNG_PREC_FP32 ? std::max(p->k, p->k_rerank) : p->k) : 10;
+    Launch L = prec == ONNG_PREC_BF16 ? pick_v<__nv_bfloat16>(d, kr)
+               : prec == ONNG_PREC_FP8 ? pick_v<__nv_fp8_e4m3>(d, kr)
+                                       : pick_v<float>(d, kr);
     int per_sm = 16;
     if (!L.fn || resident_blocks(L, &per_sm) != ONNG_OK)
         per_sm = 16;
@@ -1048,13 +1088,18 @@ static int search_impl(const onng_index *idx, const float *Q, int64_t nq, const 
     ONNG_REQUIRE(!std::isnan(p->eps) && p->eps >= 0, ONNG_E_INVAL, "onng_search: eps must be >= 0");
     ONNG_REQUIRE(idx->adj == nullptr || idx->adj_width >= 1, ONNG_E_INVAL, "onng_search: adj_width must be >= 1");
     const bool bf16 = p->precision == ONNG_PREC_BF16;
-    ONNG_REQUIRE(p->precision == ONNG_PREC_FP32 || bf16, ONNG_E_INVAL, "onng_search: unknown precision");
+    const bool fp8 = p->precision == ONNG_PREC_FP8;
+    ONNG_REQUIRE(p->precision == ONNG_PREC_FP32 || bf16 || fp8, ONNG_E_INVAL, "onng_search: unknown precision");
     int kr = p->k;
-    if (bf16) {
+    if (bf16 || fp8) {
         kr = std::max(p->k, p->k_rerank);
         ONNG_REQUIRE(kr <= kMaxK, ONNG_E_UNSUPPORTED, "onng_search: k_rerank > %d", kMaxK);
-        ONNG_REQUIRE(idx->X_bf16 && aligned16(idx->X_bf16), ONNG_E_INVAL, "onng_search: bf16 needs aligned X_bf16");
     }
+    if (bf16)
+        ONNG_REQUIRE(idx->X_bf16 && aligned16(idx->X_bf16), ONNG_E_INVAL, "onng_search: bf16 needs aligned X_bf16");
+    if (fp8)
+        ONNG_REQUIRE(idx->X_fp8 && aligned16(idx->X_fp8) && idx->fp8_scale && aligned16(idx->fp8_scale),
+                     ONNG_E_INVAL, "onng_search: fp8 needs aligned X_fp8 and fp8_scale");
     if (nq == 0)
         return ONNG_OK;
     ONNG_REQUIRE(idx->row_ptr && idx->col && idx->X && Q && seeds && (feat || (out_ids && out_dist)), ONNG_E_INVAL,
@@ -1062,7 +1107,9 @@ static int search_impl(const onng_index *idx, const float *Q, int64_t nq, const 
     ONNG_REQUIRE(aligned16(idx->X) && aligned16(Q), ONNG_E_INVAL, "onng_search: X and Q must be 16-byte aligned");
     ONNG_REQUIRE(ws, ONNG_E_WORKSPACE, "onng_search: NULL workspace");
 
-    Launch L = bf16 ? pick_v<__nv_bfloat16>(idx->d, kr) : pick_v<float>(idx->d, kr);
+    Launch L = bf16  ? pick_v<__nv_bfloat16>(idx->d, kr)
+               : fp8 ? pick_v<__nv_fp8_e4m3>(idx->d, kr)
+                     : pick_v<float>(idx->d, kr);
     ONNG_REQUIRE(L.fn, ONNG_E_UNSUPPORTED, "onng_search: no kernel for d=%d", idx->d);
     int per_sm = 0;
     int st = resident_blocks(L, &per_sm);
@@ -1090,6 +1137,8 @@ static int search_impl(const onng_index *idx, const float *Q, int64_t nq, const 
     a.adj_w = idx->adj_width;
     a.X = idx->X;
     a.Xb = idx->X_bf16;
+    a.X8 = idx->X_fp8;
+    a.scale8 = idx->fp8_scale;
     a.n = idx->n;
     a.d = idx->d;
     a.Q = Q;

@@ -21,7 +21,7 @@ _lib = None
 
 ONNG_OK, ONNG_E_INVAL, ONNG_E_WORKSPACE, ONNG_E_CUDA, ONNG_E_LIMIT, ONNG_E_UNSUPPORTED = range(6)
 FLAG_S_OVERFLOW, FLAG_VISIT_OVERFLOW, FLAG_LIMIT = 1, 2, 4
-PREC_FP32, PREC_BF16 = 0, 1
+PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 
 
 class OnngError(RuntimeError):
@@ -32,7 +32,8 @@ class OnngError(RuntimeError):
 
 class _Index(C.Structure):
     _fields_ = [("row_ptr", C.c_void_p), ("col", C.c_void_p), ("X", C.c_void_p), ("X_bf16", C.c_void_p),
-                ("adj", C.c_void_p), ("n", C.c_int64), ("d", C.c_int32), ("adj_width", C.c_int32)]
+                ("adj", C.c_void_p), ("n", C.c_int64), ("d", C.c_int32), ("adj_width", C.c_int32),
+                ("X_fp8", C.c_void_p), ("fp8_scale", C.c_void_p)]
 
 
 class _Params(C.Structure):
@@ -74,6 +75,7 @@ def load(build_if_missing: bool = True):
             "onng_search": ([C.POINTER(_Index), vp, i64, C.POINTER(_Params), vp, i32, vp, vp, vp, vp, vp, vp, sz, vp],
                             C.c_int),
             "onng_to_bf16": ([vp, i64, vp, vp], C.c_int),
+            "onng_to_fp8": ([vp, i64, i32, vp, vp, vp], C.c_int),
             "onng_pad_adjacency": ([vp, vp, i64, i32, vp, vp], C.c_int),
             "onng_search_probe": ([C.POINTER(_Index), vp, i64, C.POINTER(_Params), vp, i32, f32, vp, vp, vp, sz, vp],
                                   C.c_int),
@@ -102,7 +104,7 @@ def exported_symbols():
         "onng_adjust_path_workspace_bytes", "onng_adjust_path", "onng_seeds_random",
         "onng_seeds_pivot_workspace_bytes", "onng_seeds_pivot", "onng_search_workspace_bytes", "onng_search",
         "onng_to_bf16", "onng_pad_adjacency", "onng_search_probe", "onng_mlp_nparam", "onng_mlp_forward",
-        "onng_mlp_loss_grad", "onng_mlp_adam", "onng_mlp_train", "onng_mlp_predict", "onng_search_noalloc",
+        "onng_mlp_loss_grad", "onng_mlp_adam", "onng_mlp_train", "onng_mlp_predict", "onng_search_noalloc", "onng_to_fp8",
     ]
 
 
@@ -237,6 +239,17 @@ def to_bf16(X: torch.Tensor) -> torch.Tensor:
     return out
 
 
+def to_fp8(X: torch.Tensor):
+    """(scale float32 [d], codes uint8 [n, d]): the library's e4m3 copy with
+    per-dimension scales max|x_j| / 448."""
+    X = _dev(X, torch.float32)
+    n, d = X.shape
+    scale = torch.empty(d, dtype=torch.float32, device=X.device)
+    out = torch.empty((n, d), dtype=torch.uint8, device=X.device)
+    _check(load().onng_to_fp8(_ptr(X), n, d, _ptr(scale), _ptr(out), _stream()))
+    return scale, out
+
+
 # ----------------------------------------------------------------------------- search
 
 @dataclass
@@ -248,6 +261,8 @@ class Index:
     X_bf16: torch.Tensor | None = None
     length: torch.Tensor | None = None
     adj: torch.Tensor | None = None
+    X_fp8: torch.Tensor | None = None
+    fp8_scale: torch.Tensor | None = None
 
     @property
     def n(self) -> int:
@@ -262,6 +277,11 @@ class Index:
             self.X_bf16 = to_bf16(self.X)
         return self
 
+    def with_fp8(self) -> "Index":
+        if self.X_fp8 is None:
+            self.fp8_scale, self.X_fp8 = to_fp8(self.X)
+        return self
+
     def with_adjacency(self, width: int) -> "Index":
         """Adds the padded first-`width` adjacency table the search reads when e_s <= width."""
         if self.adj is None or self.adj.shape[1] != width:
@@ -272,7 +292,9 @@ class Index:
         return _Index(self.row_ptr.data_ptr(), self.col.data_ptr(), self.X.data_ptr(),
                       0 if self.X_bf16 is None else self.X_bf16.data_ptr(),
                       0 if self.adj is None else self.adj.data_ptr(), self.n, self.d,
-                      0 if self.adj is None else self.adj.shape[1])
+                      0 if self.adj is None else self.adj.shape[1],
+                      0 if self.X_fp8 is None else self.X_fp8.data_ptr(),
+                      0 if self.fp8_scale is None else self.fp8_scale.data_ptr())
 
 
 def build_index(X: torch.Tensor, k: int, e_o: int, e_i: int, path: bool = True) -> Index:
@@ -312,6 +334,8 @@ def search(index: Index, Q: torch.Tensor, k: int, e_s: int, eps: float, seeds: t
     lib = load()
     if precision == PREC_BF16:
         index.with_bf16()
+    elif precision == PREC_FP8:
+        index.with_fp8()
     p = _Params(k, e_s, float(eps) if math.isfinite(eps) else math.inf, precision, k_rerank, max_expansions)
     ic = index._c()
     need = lib.onng_search_workspace_bytes(nq, C.byref(ic), C.byref(p))
@@ -347,6 +371,8 @@ def search_noalloc(index: Index, Q: torch.Tensor, k: int, e_s: int, eps: float, 
     lib = load()
     if precision == PREC_BF16:
         index.with_bf16()
+    elif precision == PREC_FP8:
+        index.with_fp8()
     p = _Params(k, e_s, float(eps) if math.isfinite(eps) else math.inf, precision, k_rerank, max_expansions)
     ic = index._c()
     if out is None:

@@ -328,6 +328,44 @@ def test_search_bf16_rerank(onng, sift_graph):
     assert np.array_equal(host(st)[:, 0], o_st[:, 0])
 
 
+@pytest.mark.parametrize("name,n", [("sift1m", 20000), ("gmm10k", 5000)])
+def test_to_fp8_matches_oracle(onng, name, n):
+    """Per-dimension scales and e4m3 codes: the same float32 division and the
+    same rounding decision on both sides, so both are bit-exact."""
+    X, _ = synth.workload(name, n=n, nq=1)
+    X[:, 3] = 0.0  # an all-zero column takes scale 1
+    scale, codes = onng.to_fp8(dev(X))
+    o_scale, o_codes, _ = oracle.fp8_quantize(X)
+    assert np.array_equal(host(scale), o_scale)
+    assert np.array_equal(host(codes), o_codes)
+
+
+@pytest.mark.parametrize("name", ["sift1m", "gmm10k"])
+def test_search_fp8_follows_oracle_on_dequantised_vectors(onng, name):
+    """The FP8 pass follows the oracle run on the dequantised vectors
+    scale_j * e4m3 (float32 products), then the float32 rerank of k_rerank
+    candidates against the exact vectors."""
+    X, Q = synth.workload(name, n=4000, nq=150)
+    nbr, ln = onng.build_knng(dev(X), 30)
+    g = onng.adjust_path(*onng.adjust_degree(nbr, ln, 10, 20))
+    seeds = onng.seeds_pivot(dev(X), dev(Q), 512, 10)
+    idx = onng.Index(g[0], g[1], dev(X))
+    ids, dist, st = onng.search(idx, dev(Q), 10, 10, 0.05, seeds, precision=onng.PREC_FP8, k_rerank=32)
+    _, _, xq = oracle.fp8_quantize(X)
+    o_ids, _, o_st = oracle.search(host(g[0]), host(g[1]), xq, Q, 32, 10, np.float32(0.05), host(seeds))
+    d64 = np.linalg.norm(X[o_ids].astype(np.float64) - Q[:, None, :].astype(np.float64), axis=2)
+    order = np.lexsort((o_ids, d64), axis=1)[:, :10]
+    want = np.take_along_axis(o_ids, order, 1)
+    same = (host(ids) == want).all(1)
+    assert same.mean() >= 0.95
+    # same work where the runs agree: the distance-computation counts match on most queries
+    assert (host(st)[:, 0] == o_st[:, 0]).mean() >= 0.9
+    # returned distances are exact float32 distances to the returned ids
+    ok = host(ids) >= 0
+    d32 = np.linalg.norm(X[np.where(ok, host(ids), 0)] - Q[:, None, :], axis=2)
+    np.testing.assert_allclose(host(dist)[ok], d32[ok], rtol=1e-5)
+
+
 def test_search_bf16_float_data(onng):
     """On float data the bf16 pass follows the oracle run on bf16-rounded vectors;
     the rerank then uses the exact vectors."""
