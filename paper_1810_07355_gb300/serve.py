@@ -109,7 +109,8 @@ class Server:
                  precision: int = onng.PREC_FP32, k_rerank: int = 0, slots: int = 4, ws_budget: int = 1 << 30,
                  max_queries: int = 4096, k_max: int = 100):
         self.lib = onng.load()
-        self.index = index.with_bf16() if precision == onng.PREC_BF16 else index
+        self.index = (index.with_bf16() if precision == onng.PREC_BF16 else
+                      index.with_fp8() if precision == onng.PREC_FP8 else index)
         self.eps_table, self.e_s = dict(eps_table), e_s
         self.n_pivot, self.n_seed = n_pivot, n_seed
         self.precision, self.k_rerank = precision, k_rerank
@@ -268,8 +269,9 @@ def main():
     ap.add_argument("--rate", type=float, default=100_000.0, help="mean offered queries/s")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--ws-mb", type=int, default=1024, help="device workspace budget over all slots (MB)")
-    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--e-s", type=int, default=10, help="first e_s tried per class (then 2x, 4x, every edge)")
+    ap.add_argument("--k-rerank", type=int, default=32, help="float32 rerank of max(k, this) in bf16 / fp8")
     ap.add_argument("--capacity-rate", type=float, default=2_000_000.0,
                     help="offered load of a second, saturating run (0: skip)")
     a = ap.parse_args()
@@ -282,13 +284,14 @@ def main():
     nbr, ln = onng.build_knng(Xd, 40)
     g = onng.adjust_path(*onng.adjust_degree(nbr, ln, 10, 30))
     index = onng.Index(g[0], g[1], Xd).with_adjacency(a.e_s)
-    prec = onng.PREC_BF16 if a.precision == "bf16" else onng.PREC_FP32
+    prec = {"fp32": onng.PREC_FP32, "bf16": onng.PREC_BF16, "fp8": onng.PREC_FP8}[a.precision]
     ks, recalls = (1, 10, 100), (0.9, 0.95, 0.99)
     es_opts = (a.e_s, 2 * a.e_s, 4 * a.e_s, 0)
-    table = calibrate_eps(index, Qcal, ks, recalls, es_opts, 256, 10, prec, 0)
+    kr = a.k_rerank if prec != onng.PREC_FP32 else 0
+    table = calibrate_eps(index, Qcal, ks, recalls, es_opts, 256, 10, prec, kr)
     table32 = calibrate_eps(index, Qcal, ks, recalls, es_opts, 256, 10)
     budget = a.ws_mb << 20
-    srv = Server(index, table, a.e_s, precision=prec, slots=a.slots, ws_budget=budget)
+    srv = Server(index, table, a.e_s, precision=prec, k_rerank=kr, slots=a.slots, ws_budget=budget)
     srv.run(trace[: min(len(trace), 200)], Q)  # warm-up
     res = srv.run(trace, Q)
     base = Server(index, table32, a.e_s, slots=1, ws_budget=budget)
@@ -312,7 +315,7 @@ def main():
             "index": "gmm10k n=10000 d=128 (k=40 graph, e_o=10, e_i=30, path adjustment)",
             "trace": {"seconds": a.seconds, "offered_qps": a.rate, "requests": len(trace), "queries": queries,
                       "sizes": "log-uniform 1..256", "k": list(ks), "recall": list(recalls)},
-            "served": dict(res.summary(trace), precision=a.precision, slots=a.slots, ws_mb=a.ws_mb,
+            "served": dict(res.summary(trace), precision=a.precision, k_rerank=kr, slots=a.slots, ws_mb=a.ws_mb,
                            ws_bytes_per_slot=srv.ws_bytes),
             "batched_fp32_one_slot": res0.summary(trace), "capacity": capacity,
             "eps_e_s_table": {f"k={k},recall={t}": [round(v[0], 4), v[1]] for (k, t), v in table.items()},

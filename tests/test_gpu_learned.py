@@ -169,3 +169,41 @@ def test_learned_search_trains_and_runs(onng, graph):
     d = host(dist)
     assert (np.diff(d, axis=1) >= 0).all() and (host(ids) >= 0).all()
     assert (host(es_q) >= 6).all() and (host(es_q) <= 20).all()
+
+
+def test_learned_gain_over_fixed_policy(onng):
+    """What the trained network gains over the method without it, measured on
+    held-out queries at a target mean recall: the cost (distance computations per
+    query, probe included) of the network's policy for every shrinkage beta
+    against one global eps.  The chosen policy reaches the target and never costs
+    more than the fixed one (the fixed policy is a candidate).  The rank
+    correlation of the network's eps with the held-out label eps is printed: on
+    this workload it is near zero, and the choice falls back to the fixed eps."""
+    from scipy.stats import spearmanr
+
+    from paper_1810_07355_gb300 import learned
+    X, Q = synth.workload("sift1m", n=20000, nq=1200)
+    nbr, ln = onng.build_knng(dev(X), 40)
+    g = onng.adjust_path(*onng.adjust_degree(nbr, ln, 10, 30))
+    idx = onng.Index(g[0], g[1], dev(X)).with_adjacency(20)
+    Qd = dev(Q)
+    gt, _ = onng.knn(dev(X), Qd, 10)
+    seeds = onng.seeds_pivot(dev(X), Qd, 512, 10)
+    tr, ho = slice(0, 800), slice(800, 1200)
+    pred, _ = learned.train(idx, Qd[tr], gt[tr], seeds[tr], 10, targets=(0.9, 1.0), h=4, steps=2000)
+    best, ybar, table = learned.select_shrinkage(pred, idx, Qd[ho], gt[ho], seeds[ho], 10, 0.9, 1.0,
+                                                 es_options=(20,), precision=onng.PREC_FP32)
+    fixed = [r for r in table if r["beta"] is None][0]
+    print("\nbeta  dc/query  recall")
+    for r in table:
+        print(r["beta"], round(r["dc"], 1), round(r["recall"], 4))
+    assert best is not None and best["recall"] >= 0.9 - 1e-9
+    assert best["dc"] <= fixed["dc"] + 1e-9
+    # the network's own eps (beta = 1) against the held-out labels
+    rec, cost = learned.sweep(idx, Qd[ho], gt[ho], seeds[ho], 10)
+    eps_lab, _ = learned.labels_from_sweep(rec, cost, 1.0)
+    feat, _ = onng.search_probe(idx, Qd[ho], 10, pred.probe_es, 0.0, seeds[ho], pred.h, 1.0)
+    y = onng.mlp_forward(pred.P, feat)[:, 0]
+    rho = spearmanr(host(y), host(eps_lab)).correlation
+    print("held-out rank correlation of predicted and label eps:", round(float(rho), 3))
+    assert np.isfinite(rho)
