@@ -49,7 +49,7 @@ def test_serving_results_equal_alone_and_in_the_mix():
     g = onng.adjust_path(*onng.adjust_degree(nbr, ln, 10, 30))
     index = onng.Index(g[0], g[1], Xd).with_adjacency(10)
     eps = {(k, r): e for k in (1, 10, 100) for r, e in ((0.9, 0.02), (0.95, 0.05), (0.99, 0.1))}
-    for prec in (onng.PREC_FP32, onng.PREC_BF16):
+    for prec in (onng.PREC_FP32, onng.PREC_BF16, onng.PREC_FP8):
         # a small workspace budget: three slots with clamped grids
         srv = Server(index, eps, 10, precision=prec, k_rerank=20 if prec else 0, slots=3, ws_budget=48 << 20,
                      max_queries=1024)
