@@ -838,7 +838,7 @@ void oracle_bf16_round(const float *x, int64_t m, float *y)
 }
 
 /*
- * FP8 e4m3 with per-dimension scales (a spec precision form; the paper is
+ * FP8 e4m3 with per-dimension scales (a reduced-precision form of the library; the paper is
  * silent).  e4m3 here is the finite variant: 1 sign, 4 exponent (bias 7) and 3
  * mantissa bits, no infinities, 0x7F / 0xFF are NaN, largest finite 448;
  * subnormals are m * 2^-9.  Reading for the scales: c_j = max_i |x_ij| / 448 in
