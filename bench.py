@@ -439,7 +439,7 @@ def cpu_baseline(a, idx, X, Q, seeds, eps, sample=2000):
 
 
 def reference_arm(a, idx, X, Q, seeds, eps, config, world):
-    """Times the CPU oracle's search (the reference for this build) on the host cores."""
+    """Times the CPU oracle's search (the reference arm) on the host cores."""
     import oracle
     oracle.build()
     ptr = idx.row_ptr.cpu().numpy()
