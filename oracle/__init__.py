@@ -72,6 +72,8 @@ def _load():
             lib.oracle_search_probe.restype = i32
             lib.oracle_bf16_round.argtypes = [vp, i64, vp]
             lib.oracle_bf16_round.restype = None
+            lib.oracle_adjust_degree_sac.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, vp, i64]
+            lib.oracle_adjust_degree_sac.restype = i64
             lib.oracle_e4m3_encode.argtypes = [vp, i64, vp]
             lib.oracle_e4m3_encode.restype = None
             lib.oracle_e4m3_decode.argtypes = [vp, i64, vp]
@@ -136,6 +138,20 @@ def adjust_degree(nbr, length, e_o: int, e_i: int, rows=None):
     ln = np.empty(cap, np.float64)
     m = _load().oracle_adjust_degree(_p(nbr), _p(length), n, k, e_o, e_i,
                                      None if r is None else _p(r), nrows, _p(ptr), _p(col), _p(ln), cap)
+    assert m >= 0
+    return ptr, col[:m].copy(), ln[:m].copy()
+
+
+def adjust_degree_sac(nbr, length, e_o: int, e_i: int):
+    """Algorithm 3 (degree adjustment with constraints).  CSR (ptr, col, len float64)."""
+    nbr = _c(nbr, np.int32)
+    length = _c(length, np.float64)
+    n, k = nbr.shape
+    cap = int(n) * (min(e_i, k) + min(e_o, k)) + 1
+    ptr = np.empty(n + 1, np.int64)
+    col = np.empty(cap, np.int32)
+    ln = np.empty(cap, np.float64)
+    m = _load().oracle_adjust_degree_sac(_p(nbr), _p(length), n, k, e_o, e_i, _p(ptr), _p(col), _p(ln), cap)
     assert m >= 0
     return ptr, col[:m].copy(), ln[:m].copy()
 

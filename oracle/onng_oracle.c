@@ -16,6 +16,7 @@
  *   oracle_knn            exact k-nearest neighbours (textbook definition; the
  *                         exact graph replaces the paper's ANNG-derived AKNNG, Sec. 2.5)
  *   oracle_adjust_degree  static degree adjustment, Algorithm 2 (set form, Sec. 2.1)
+ *   oracle_adjust_degree_sac  degree adjustment with constraints, Algorithm 3
  *   oracle_adjust_path    path adjustment, Algorithms 4/5 read order-free (Sec. 2.3)
  *   oracle_adjust_path_alg4  Algorithm 4 taken literally (round-robin, ascending ids)
  *   oracle_search         KnnSearch, Algorithm 1, with the visited set of
@@ -251,6 +252,151 @@ int64_t oracle_adjust_degree(const int32_t *nbr, const double *len, int64_t n, i
     free(incnt);
     free(slot);
     return ret == 0 ? w : -1;
+}
+
+/*
+ * Algorithm 3 (ConstructAdjustedGraphWithConstraint, "SAC"): degree adjustment
+ * with constraints, a sequential greedy pass.
+ *   1. G_t is Algorithm 2 with (0, e_i): N(G_t, x) = { y : x in first_{e_i}(N_k(y)) }.
+ *   2. Nodes o are taken in increasing |N(G_t, o)|; for each, the members n of
+ *      N(G_t, o) in increasing d(n, o): the edge o->n is added when n has no
+ *      incoming edge yet, or when n has fewer than e_i incoming edges and o fewer
+ *      than e_o outgoing ones.
+ *   3. Every node o then takes its nearest kNN neighbours not yet in its list
+ *      while it has fewer than e_o edges.
+ * Readings (the paper is silent): ties in the argmin over |N(G_t, x)| go to the
+ * smaller id (G_t never changes, so the order is the sort by (|N(G_t, x)|, x));
+ * ties in d(x, o) go to the smaller id; the second loop's bound "N(G_e, o) < e_o"
+ * is read as |N(G_e, o)| < e_o; an edge o->n of step 2 carries the stored length
+ * of n->o.  Rows of the result are sorted by (length, id) like Algorithm 2's.
+ * Output CSR out_ptr [n + 1], out_col / out_len of capacity cap; returns the
+ * number of edges, or -1 (bad argument, cap too small, no memory).
+ */
+typedef struct {
+    int64_t key;
+    int64_t id;
+} order_t;
+
+static int cmp_order(const void *a, const void *b)
+{
+    const order_t *x = (const order_t *)a, *y = (const order_t *)b;
+    if (x->key != y->key)
+        return (x->key > y->key) - (x->key < y->key);
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+int64_t oracle_adjust_degree_sac(const int32_t *nbr, const double *len, int64_t n, int k, int e_o, int e_i,
+                                 int64_t *out_ptr, int32_t *out_col, double *out_len, int64_t cap)
+{
+    if (n < 0 || k <= 0 || e_o < 0 || e_i < 0)
+        return -1;
+    const int fi = e_i < k ? e_i : k;
+    const int fo = e_o < k ? e_o : k;
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    int64_t *tptr = (int64_t *)calloc(nn + 1, sizeof(int64_t));
+    int64_t *tfill = (int64_t *)calloc(nn, sizeof(int64_t));
+    int64_t *icnt = (int64_t *)calloc(nn, sizeof(int64_t));
+    int64_t *ecnt = (int64_t *)calloc(nn, sizeof(int64_t));
+    int64_t *eptr = (int64_t *)calloc(nn + 1, sizeof(int64_t));
+    order_t *ord = (order_t *)malloc(nn * sizeof(order_t));
+    int64_t ret = -1;
+    edge_t *tl = NULL, *el = NULL, *sbuf = NULL;
+    if (!tptr || !tfill || !icnt || !ecnt || !eptr || !ord)
+        goto done;
+    /* G_t: the transposed first-e_i lists */
+    for (int64_t y = 0; y < n; ++y)
+        for (int p = 0; p < fi; ++p) {
+            const int32_t x = nbr[y * k + p];
+            if (x >= 0)
+                tptr[x + 1]++;
+        }
+    for (int64_t x = 0; x < n; ++x)
+        tptr[x + 1] += tptr[x];
+    tl = (edge_t *)malloc((size_t)(tptr[n] > 0 ? tptr[n] : 1) * sizeof(edge_t));
+    /* G_e: room for every step-2 edge of o (at most |N(G_t, o)|) plus e_o more */
+    for (int64_t o = 0; o < n; ++o)
+        eptr[o + 1] = eptr[o] + (tptr[o + 1] - tptr[o]) + fo;
+    el = (edge_t *)malloc((size_t)(eptr[n] > 0 ? eptr[n] : 1) * sizeof(edge_t));
+    int64_t maxdeg = 0;
+    for (int64_t x = 0; x < n; ++x)
+        maxdeg = tptr[x + 1] - tptr[x] > maxdeg ? tptr[x + 1] - tptr[x] : maxdeg;
+    sbuf = (edge_t *)malloc((size_t)(maxdeg > 0 ? maxdeg : 1) * sizeof(edge_t));
+    if (!tl || !el || !sbuf)
+        goto done;
+    for (int64_t y = 0; y < n; ++y)
+        for (int p = 0; p < fi; ++p) {
+            const int32_t x = nbr[y * k + p];
+            if (x >= 0) {
+                tl[tptr[x] + tfill[x]].id = (int32_t)y;
+                tl[tptr[x] + tfill[x]].len = len[y * k + p];
+                tfill[x]++;
+            }
+        }
+    for (int64_t x = 0; x < n; ++x) {
+        ord[x].key = tptr[x + 1] - tptr[x];
+        ord[x].id = x;
+    }
+    qsort(ord, nn, sizeof(order_t), cmp_order);
+    /* step 2: reversed edges under the degree constraints */
+    for (int64_t r = 0; r < n; ++r) {
+        const int64_t o = ord[r].id;
+        const int64_t m = tptr[o + 1] - tptr[o];
+        memcpy(sbuf, tl + tptr[o], (size_t)m * sizeof(edge_t));
+        qsort(sbuf, (size_t)m, sizeof(edge_t), cmp_edge);
+        for (int64_t t = 0; t < m; ++t) {
+            const int32_t nd = sbuf[t].id;
+            if (icnt[nd] == 0 || (icnt[nd] < e_i && ecnt[o] < e_o)) {
+                el[eptr[o] + ecnt[o]] = sbuf[t];
+                ecnt[o]++;
+                icnt[nd]++;
+            }
+        }
+    }
+    /* step 3: the nearest kNN neighbours up to e_o edges */
+    for (int64_t o = 0; o < n; ++o)
+        for (int p = 0; p < k && ecnt[o] < e_o; ++p) {
+            const int32_t x = nbr[o * k + p];
+            if (x < 0)
+                break;
+            int have = 0;
+            for (int64_t u = 0; u < ecnt[o]; ++u)
+                if (el[eptr[o] + u].id == x) {
+                    have = 1;
+                    break;
+                }
+            if (!have) {
+                el[eptr[o] + ecnt[o]].id = x;
+                el[eptr[o] + ecnt[o]].len = len[o * k + p];
+                ecnt[o]++;
+            }
+        }
+    {
+        int64_t w = 0;
+        out_ptr[0] = 0;
+        for (int64_t o = 0; o < n; ++o) {
+            if (w + ecnt[o] > cap)
+                goto done;
+            qsort(el + eptr[o], (size_t)ecnt[o], sizeof(edge_t), cmp_edge);
+            for (int64_t u = 0; u < ecnt[o]; ++u) {
+                out_col[w] = el[eptr[o] + u].id;
+                out_len[w] = el[eptr[o] + u].len;
+                ++w;
+            }
+            out_ptr[o + 1] = w;
+        }
+        ret = w;
+    }
+done:
+    free(tptr);
+    free(tfill);
+    free(icnt);
+    free(ecnt);
+    free(eptr);
+    free(ord);
+    free(tl);
+    free(el);
+    free(sbuf);
+    return ret;
 }
 
 /* ------------------------------------------------------ path adjustment (O3) */

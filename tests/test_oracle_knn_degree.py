@@ -143,3 +143,57 @@ def test_degree_row_subset(oracle_lib, small_graph):
         a = full[1][full[0][i]:full[0][i + 1]]
         b = col[ptr[r]:ptr[r + 1]]
         assert np.array_equal(a, b)
+
+
+def _rows(ptr, col, ln):
+    return [list(zip(col[ptr[i]:ptr[i + 1]].tolist(), ln[ptr[i]:ptr[i + 1]].tolist())) for i in range(len(ptr) - 1)]
+
+
+def test_sac_hand_traced_line(oracle_lib):
+    """Algorithm 3 on five points of a line, x = 0, 1, 3, 6, 10, with k = 2:
+    N_k = 0:[1,2] 1:[0,2] 2:[1,0] 3:[2,4] 4:[3,2] (ties by id).
+    (e_o, e_i) = (1, 1): G_t = 0:{1} 1:{0,2} 2:{3} 3:{4} 4:{}; order 4, 0, 2, 3, 1;
+    step 2 adds 0->1, 2->3, 3->4, 1->0, 1->2 (n = 2 has no in-edge yet, so the
+    out-degree limit does not apply); step 3 gives node 4 its nearest, 3.
+    (e_o, e_i) = (1, 2): order 3, 4, 0, 1, 2; step 2 adds 3->4, 4->3, 0->1, 0->2,
+    1->0, 2->1 and skips the rest (n has an in-edge and o has e_o out-edges)."""
+    x = np.array([0.0, 1.0, 3.0, 6.0, 10.0])
+    nbr = np.array([[1, 2], [0, 2], [1, 0], [2, 4], [3, 2]], dtype=np.int32)
+    ln = np.abs(x[nbr] - x[:, None])
+    got = _rows(*oracle_lib.adjust_degree_sac(nbr, ln, 1, 1))
+    assert got == [[(1, 1.0)], [(0, 1.0), (2, 2.0)], [(3, 3.0)], [(4, 4.0)], [(3, 4.0)]]
+    got = _rows(*oracle_lib.adjust_degree_sac(nbr, ln, 1, 2))
+    assert got == [[(1, 1.0), (2, 3.0)], [(0, 1.0)], [(1, 2.0)], [(4, 4.0)], [(3, 4.0)]]
+
+
+def test_sac_special_cases_and_invariants(oracle_lib):
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=(400, 6))
+    nbr, ln = oracle_lib.knng(X.astype(np.float32), 12)
+    n = len(X)
+    # e_i = 0: no reversed edges, the result is the kNN graph truncated to e_o
+    ptr, col, l = oracle_lib.adjust_degree_sac(nbr, ln, 5, 0)
+    assert np.array_equal(ptr, np.arange(n + 1) * 5)
+    assert np.array_equal(col.reshape(n, 5), nbr[:, :5])
+    # e_o = 0: exactly one incoming edge per node, from one of its first e_i neighbours
+    ptr, col, l = oracle_lib.adjust_degree_sac(nbr, ln, 0, 4)
+    src = np.repeat(np.arange(n), np.diff(ptr))
+    assert len(col) == n and np.array_equal(np.sort(col), np.arange(n))
+    assert all(src[t] in nbr[col[t], :4] for t in range(len(col)))
+    # general case: every node has an in-edge; out-degree >= e_o; in-degree from the
+    # reversed pass is <= e_i; no self loops or duplicates; rows sorted by (len, id)
+    e_o, e_i = 4, 6
+    ptr, col, l = oracle_lib.adjust_degree_sac(nbr, ln, e_o, e_i)
+    src = np.repeat(np.arange(n), np.diff(ptr))
+    assert set(col.tolist()) == set(range(n))
+    assert np.all(np.diff(ptr) >= e_o) and np.all(col != src)
+    for i in range(n):
+        row = list(zip(l[ptr[i]:ptr[i + 1]], col[ptr[i]:ptr[i + 1]]))
+        assert row == sorted(row) and len(set(c for _, c in row)) == len(row)
+    # an edge o->n is either a kNN edge of o or a reversed edge (o among n's first e_i)
+    fwd = {(i, j) for i in range(n) for j in nbr[i]}
+    rev = {(j, i) for i in range(n) for j in nbr[i, :e_i]}
+    assert all((s, c) in fwd or (s, c) in rev for s, c in zip(src.tolist(), col.tolist()))
+    # lengths are the stored kNN lengths of the edge's pair
+    d = {(i, j): ln[i, p] for i in range(n) for p, j in enumerate(nbr[i])}
+    assert all(np.isclose(lv, d.get((s, c), d.get((c, s)))) for s, c, lv in zip(src, col, l))
