@@ -1,0 +1,44 @@
+"""Host-side pieces of the benchmark: clock-sample parsing, the algorithmic-byte
+count behind the roofline, and recall@k."""
+import types
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import bench  # noqa: E402
+
+
+def test_clock_summary_median_max_and_reasons():
+    c = bench.Clocks(0)
+    c.lines = [
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1300.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2000, 2070, 1250.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "garbage line",
+        "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    s = c.summary()
+    assert s == {"sm_mhz": 2000.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c.lines.append("0, 1500, 2070, 1300.0, 0x8, Active, Not Active, Active, Not Active")
+    assert c.summary()["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
+    assert bench.Clocks(0).summary() is None
+
+
+def test_search_bytes_closed_form():
+    # stats rows: distance computations, expansions, adjacency entries scanned, flags
+    st = torch.tensor([[100, 10, 200, 0], [50, 5, 100, 0]], dtype=torch.int32)
+    a = types.SimpleNamespace(nq=2, n_seed=10, k=10, k_rerank=20)
+    d = 128
+    b, ndc = bench.search_bytes(st, d, a, 2, True)
+    want = 150 * d * 2 + 300 * 4 + 15 * 16 + 2 * d * 4 + 2 * 10 * 4 + 2 * 10 * 8 + 2 * 20 * d * 4
+    assert b == want and ndc == 75.0
+    b32, _ = bench.search_bytes(st, d, a, 4, False)
+    assert b32 == 150 * d * 4 + 300 * 4 + 15 * 16 + 2 * d * 4 + 2 * 10 * 4 + 2 * 10 * 8
+
+
+def test_recall_at_counts_hits_and_ignores_padding():
+    ids = torch.tensor([[1, 2, 3], [4, 5, 6]])
+    gt = torch.tensor([[3, 2, 9], [4, -1, -1]])
+    # query 0: 2 of 3; query 1: 1 hit (padding never matches) -> (2/3 + 1/3) / 2
+    assert bench.recall_at(ids, gt) == pytest.approx(0.5)
+    assert bench.recall_at(gt.clamp_min(0), gt.clamp_min(0)) == pytest.approx(1.0)
