@@ -129,6 +129,22 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value: float, device) -> float:
+    """The largest value over the ranks of the process group (the slowest rank sets
+    the job's time); the value itself when there is no group or one rank."""
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    d = torch.distributed
+    if d.is_available() and d.is_initialized() and d.get_world_size() > 1:
+        d.all_reduce(t, op=d.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(queries_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job queries/s: every rank searched its own batch within ms_max."""
+    return world * queries_per_rank / (ms_max / 1e3)
+
+
 def recall_at(ids, gt):
     hit = (ids[:, :, None] == gt[:, None, :]) & (gt[:, None, :] >= 0)
     return float(hit.any(2).sum(1).float().mean().item() / gt.shape[1])
@@ -323,14 +339,8 @@ def main():
         torch.distributed.barrier()
     clocks = clk.summary()
 
-    def agg(f):
-        t = torch.tensor([float(np.mean(res[f][0]))], dtype=torch.float64, device=dev)
-        if world > 1:
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
-
-    ms = {f: agg(f) for f in forms}
-    qps = {f: world * a.nq / (ms[f] / 1e3) for f in forms}
+    ms = {f: max_over_ranks(float(np.mean(res[f][0])), dev) for f in forms}
+    qps = {f: job_throughput(a.nq, world, ms[f]) for f in forms}
     rec = {f: recall_at(res[f][2][0], gt) for f in forms}
     d = X.shape[1]
     peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
