@@ -64,3 +64,24 @@ def test_version_and_argument_checks(lib):
     assert st == onng.ONNG_E_UNSUPPORTED
     st = lib.onng_adjust_degree_count(None, None, -5, 10, 3, 3, None, None, None, 0, None)
     assert st == onng.ONNG_E_INVAL
+
+
+def test_reduced_precision_argument_checks(lib):
+    """Rejected before any CUDA call: FP8 search without its codes or scales, a
+    bf16 search without X_bf16, bad FP8 conversion arguments, unknown precision."""
+    from paper_1810_07355_gb300 import onng
+    ix = onng._Index(None, None, None, None, None, 100, 128, 0)
+    p = onng._Params(10, 10, 0.1, onng.PREC_FP8, 20, 0)
+    st = lib.onng_search(C.byref(ix), None, 5, C.byref(p), None, 4, None, None, None, None, None, None, 0, None)
+    assert st == onng.ONNG_E_INVAL and b"fp8 needs" in lib.onng_last_error()
+    p = onng._Params(10, 10, 0.1, onng.PREC_BF16, 20, 0)
+    st = lib.onng_search(C.byref(ix), None, 5, C.byref(p), None, 4, None, None, None, None, None, None, 0, None)
+    assert st == onng.ONNG_E_INVAL and b"bf16 needs" in lib.onng_last_error()
+    p = onng._Params(10, 10, 0.1, 7, 20, 0)
+    st = lib.onng_search(C.byref(ix), None, 5, C.byref(p), None, 4, None, None, None, None, None, None, 0, None)
+    assert st == onng.ONNG_E_INVAL and b"unknown precision" in lib.onng_last_error()
+    p = onng._Params(10, 10, 0.1, onng.PREC_FP8, 200, 0)
+    st = lib.onng_search(C.byref(ix), None, 5, C.byref(p), None, 4, None, None, None, None, None, None, 0, None)
+    assert st == onng.ONNG_E_UNSUPPORTED and b"k_rerank" in lib.onng_last_error()
+    assert lib.onng_to_fp8(None, -1, 8, None, None, None) == onng.ONNG_E_INVAL
+    assert lib.onng_to_fp8(None, 10, 8, None, None, None) == onng.ONNG_E_INVAL
