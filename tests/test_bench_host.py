@@ -42,3 +42,17 @@ def test_recall_at_counts_hits_and_ignores_padding():
     # query 0: 2 of 3; query 1: 1 hit (padding never matches) -> (2/3 + 1/3) / 2
     assert bench.recall_at(ids, gt) == pytest.approx(0.5)
     assert bench.recall_at(gt.clamp_min(0), gt.clamp_min(0)) == pytest.approx(1.0)
+
+
+def test_cpu_baseline_times_whole_passes(oracle_lib):
+    """The CPU baseline leg runs the oracle over whole passes of the query batch."""
+    from paper_1810_07355_gb300 import synth
+    X, Q = synth.workload("gmm10k", n=1500, nq=40)
+    nbr, ln = oracle_lib.knng(X, 10)
+    ptr, col, _ = oracle_lib.adjust_degree(nbr, ln, 5, 10)
+    seeds = torch.from_numpy(oracle_lib.seeds_pivot(X, Q, 64, 5))
+    idx = types.SimpleNamespace(row_ptr=torch.from_numpy(ptr), col=torch.from_numpy(col))
+    a = types.SimpleNamespace(k=10, e_s=10)
+    r = bench.cpu_baseline(a, idx, X, Q, seeds, 0.1, min_wall=0.05, max_reps=3)
+    assert r["kind"] == "oracle" and r["value"] > 0 and r["cores"] >= 1
+    assert "pass(es) over all 40 queries" in r["sample"]
