@@ -337,6 +337,21 @@ __device__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code)
         }
     }
 }
+// Bounded wait for a role's own work in flight before teardown: unlike
+// mbar_wait it keeps waiting when another role has already given up; on its
+// own timeout it records `code` in *err (global memory) and returns.
+__device__ void mbar_drain(uint64_t *bar, uint32_t parity, int *err, int code)
+{
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity))
+            return;
+        if ((it & 63) == 0 && global_ns() - t0 > TC_TIMEOUT_NS) {
+            atomicCAS(err, 0, code);
+            return;
+        }
+    }
+}
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int c0, int c1, uint64_t *bar)
 {
     asm volatile(
@@ -473,10 +488,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 issued = t + 1;
             }
             // our copies in flight complete before the CTA may exit (bounded)
-            int dummy = 0;
-            mbar_wait(abar, 0, &dummy, 6);
+            mbar_drain(abar, 0, err, 6);
             for (int64_t t = issued > TC_STAGES ? issued - TC_STAGES : 0; t < issued; ++t)
-                mbar_wait(&full[t % TC_STAGES], (uint32_t)((t / TC_STAGES) & 1), &dummy, 6);
+                mbar_drain(&full[t % TC_STAGES], (uint32_t)((t / TC_STAGES) & 1), err, 6);
         }
     } else if (warp == 9) {
         // ------------------------------------------------ MMA issuer
@@ -504,9 +518,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 done = t + 1;
             }
             // the MMAs issued so far complete before TMEM is freed (bounded)
-            int dummy = 0;
             if (done > 0)
-                mbar_wait(&accf[(done - 1) & 1], (uint32_t)(((done - 1) >> 1) & 1), &dummy, 7);
+                mbar_drain(&accf[(done - 1) & 1], (uint32_t)(((done - 1) >> 1) & 1), err, 7);
         }
     } else {
         // ------------------------------------------------ epilogue (warps 0-7)

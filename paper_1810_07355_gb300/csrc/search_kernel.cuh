@@ -1,0 +1,1007 @@
+// KnnSearch (Algorithm 1) on the GPU: one warp per query.  Device code of the
+// search kernels; search_inst.cu instantiates it once per (vector type, chunks
+// per lane) so the instantiations compile in parallel, and search.cu holds the
+// host entry points.
+//
+// Per warp:
+//   - the visited set C, in shared memory, as an exact open-addressing hash
+//     (linear probing).  The paper's Set/IsSet table (Sec. 2.5) keeps the first
+//     id of a bucket inline and chains collisions; on the GPU a flat table probed
+//     by 32 lanes at once is cheaper.  Past half load, new ids go to a per-warp
+//     bitmap over all n ids in global memory (one atomicOr per id, no probing);
+//     the ids set there are logged and cleared when the query ends.
+//   - the candidate set S in three levels of (distance, id) keys: a sorted head
+//     of up to 32 keys in registers (one per lane: the pop is a shift, an
+//     insertion a ballot plus a shift), an unsorted overflow of up to 256 keys in
+//     shared memory whose keys are all >= every head key, and a per-warp spill
+//     pool in global memory whose keys are all >= tau > every key above it.  So
+//     the head's first key is the minimum of S; a level refills the one above
+//     only when that one runs empty.  An entry beyond r(1+eps) can never be
+//     expanded (r only shrinks, and popping it ends the search), so such entries
+//     are dropped whenever a level is rebuilt.  S stays exact.
+//   - the result set R, in registers, as a sorted list of at most k keys.
+// The up-to-e_s neighbours of the expanded node are tested and their vectors
+// gathered together (coalesced 16-byte loads, several vectors in flight per
+// lane, one transposed butterfly reduction for all of them).  R then takes the k
+// best of R and the batch, and S takes the batch members within the new
+// r(1+eps).  Applying a batch at once yields the same R, the same r after the
+// batch and, since S only loses entries that can never be expanded, the same
+// expansion order as the one-at-a-time loop of Algorithm 1.
+//
+// The node expanded next is known as soon as the batch's distances are: it is
+// the nearer of S's head and the batch's nearest member if that one will be
+// pushed (its distance is within the bound before the batch).  Its adjacency
+// row is loaded right then, so the load overlaps the R and S updates.
+//
+// Adjacency is read from the CSR lists, or from an optional padded table
+// adj [n, width] (-1 padded) that holds each node's first `width` entries, which
+// saves the row-pointer indirection per expansion.
+//
+// Distances are squared float32 sums of (q - x)^2; bounds are compared in
+// double: d^2 <= r^2 (1 + eps)^2.  For integer-valued inputs with squared
+// distances below 2^24 every decision then equals the float64 algorithm's.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <type_traits>
+
+#include "common.cuh"
+#include "warp_sort.cuh"
+
+#ifndef ONNG_SEARCH_HV
+#define ONNG_SEARCH_HV 2048
+#endif
+#ifndef ONNG_SEARCH_MAXV
+#define ONNG_SEARCH_MAXV 8  // kernels are built for d <= 128 * ONNG_SEARCH_MAXV (1, 2, 4 or 8)
+#endif
+// Per vector type, for d <= 256 and k <= 32: shared-memory overflow keys per
+// warp (a multiple of 64), the most vectors gathered per round (a power of two)
+// and the resident CTAs per SM the registers are sized for.  Float32 vectors
+// (512 B at d = 128) want 16 gathers in flight per lane; bfloat16 vectors are
+// half the size, so fewer gathers per round and more warps per SM pay more.
+#ifndef ONNG_SEARCH_F32_OVF
+#define ONNG_SEARCH_F32_OVF 256
+#endif
+#ifndef ONNG_SEARCH_F32_GMAX
+#define ONNG_SEARCH_F32_GMAX 16
+#endif
+#ifndef ONNG_SEARCH_F32_MINB
+#define ONNG_SEARCH_F32_MINB 4
+#endif
+#ifndef ONNG_SEARCH_BF16_OVF
+#define ONNG_SEARCH_BF16_OVF 128
+#endif
+#ifndef ONNG_SEARCH_BF16_GMAX
+#define ONNG_SEARCH_BF16_GMAX 8
+#endif
+#ifndef ONNG_SEARCH_BF16_MINB
+#define ONNG_SEARCH_BF16_MINB 6
+#endif
+#ifndef ONNG_SEARCH_FP8_OVF
+#define ONNG_SEARCH_FP8_OVF 128
+#endif
+#ifndef ONNG_SEARCH_FP8_GMAX
+#define ONNG_SEARCH_FP8_GMAX 8
+#endif
+#ifndef ONNG_SEARCH_FP8_MINB
+#define ONNG_SEARCH_FP8_MINB 6
+#endif
+
+namespace onng {
+namespace sk {
+
+typedef unsigned long long u64;
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kWarpsPerCta = 4;
+constexpr int kMaxK = 128;
+constexpr int kMaxSeed = 64;
+template <class T> struct Tune {
+    static constexpr int ovf = ONNG_SEARCH_F32_OVF, gmax = ONNG_SEARCH_F32_GMAX, minb = ONNG_SEARCH_F32_MINB;
+};
+template <> struct Tune<__nv_bfloat16> {
+    static constexpr int ovf = ONNG_SEARCH_BF16_OVF, gmax = ONNG_SEARCH_BF16_GMAX, minb = ONNG_SEARCH_BF16_MINB;
+};
+template <> struct Tune<__nv_fp8_e4m3> {
+    static constexpr int ovf = ONNG_SEARCH_FP8_OVF, gmax = ONNG_SEARCH_FP8_GMAX, minb = ONNG_SEARCH_FP8_MINB;
+};
+constexpr int kVisitLog = 16384;     // ids logged per warp for clearing its bitmap
+constexpr int kGlobalPool = 16384;   // per-warp candidate spill pool entries
+constexpr u64 kMaxKey = ~0ull;
+constexpr int kFeat = 16;
+
+struct SearchArgs {
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const int32_t *adj;
+    int adj_w;
+    const float *X;
+    const uint16_t *Xb;
+    const uint8_t *X8;     // e4m3 codes, dequantised as scale8[j] * e4m3
+    const float *scale8;
+    int64_t n;
+    int d;
+    const float *Q;
+    int64_t nq;
+    int k;      // results kept by the search (k_rerank for bf16)
+    int k_out;  // results written
+    int e_s;
+    float eps;
+    const float *eps_q;
+    const int32_t *es_q;
+    const int32_t *seeds;
+    int n_seed;
+    int max_exp;
+    int32_t *out_ids;  // may be NULL (probe only)
+    float *out_dist;
+    int32_t *stats;
+    float *feat;       // [nq, kFeat] probe features, or NULL
+    float target;      // feature 0 (the recall the prediction is for)
+    int *counter;
+    unsigned *gbits;  // [slots, bits_words]: visited bitmap past the shared table
+    int64_t bits_words;
+    int *glog;        // [slots, kVisitLog]: ids set in the bitmap
+    u64 *gpool;       // [slots, kGlobalPool]
+};
+
+template <int HV, int OVF> struct WarpSmem {
+    int vis[HV];
+    u64 ovf[OVF];
+};
+
+__host__ __device__ constexpr int log2i(int v) { return v <= 1 ? 0 : 1 + log2i(v >> 1); }
+
+__device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
+
+__device__ __forceinline__ unsigned hash_id(int id) { return static_cast<unsigned>(id) * 0x9E3779B1u; }
+
+__device__ __forceinline__ float key_d2(u64 k) { return __uint_as_float((unsigned)(k >> 32)); }
+__device__ __forceinline__ int key_id(u64 k) { return (int)(unsigned)(k & 0xFFFFFFFFull); }
+
+__device__ __forceinline__ u64 warp_min_u64(u64 v)
+{
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        u64 o = __shfl_xor_sync(FULL, v, off);
+        v = o < v ? o : v;
+    }
+    return v;
+}
+
+// Ascending list of 32*N keys striped over the warp: element e sits in v[e / 32]
+// of lane e % 32.  Empty slots hold kMaxKey.
+template <int N> struct RegList {
+    u64 v[N];
+
+    __device__ void clear()
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            v[i] = kMaxKey;
+    }
+    // number of elements smaller than key
+    __device__ int rank(u64 key) const
+    {
+        int r = 0;
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            r += __popc(__ballot_sync(FULL, v[i] < key));
+        return r;
+    }
+    // element e (uniform e < 32*N), broadcast to all lanes
+    __device__ u64 get(int e) const
+    {
+        u64 x = kMaxKey;
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if (i == (e >> 5))
+                x = v[i];
+        return __shfl_sync(FULL, x, e & 31);
+    }
+    // inserts key at position pos (uniform); elements at positions >= limit are emptied
+    __device__ void insert_at(int pos, u64 key, int lane, int limit)
+    {
+        u64 carry = kMaxKey;  // old element i*32 - 1
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const u64 up = __shfl_up_sync(FULL, v[i], 1);
+            const u64 last = __shfl_sync(FULL, v[i], 31);
+            const u64 before = lane == 0 ? carry : up;
+            const int e = i * 32 + lane;
+            u64 nv = e < pos ? v[i] : (e == pos ? key : before);
+            v[i] = e < limit ? nv : kMaxKey;
+            carry = last;
+        }
+    }
+    // removes element 0
+    __device__ void pop_front(int lane)
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const u64 down = __shfl_down_sync(FULL, v[i], 1);
+            const u64 next0 = (i + 1 < N) ? __shfl_sync(FULL, v[i + 1], 0) : kMaxKey;
+            v[i] = lane == 31 ? next0 : down;
+        }
+    }
+    // empties every element at position >= m
+    __device__ void truncate(int m, int lane)
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if (i * 32 + lane >= m)
+                v[i] = kMaxKey;
+    }
+};
+
+// Loads 4 consecutive coordinates of a stored vector as float4.
+template <class T> struct Loader;
+template <> struct Loader<float> {
+    static __device__ __forceinline__ float4 load(const void *base, int64_t id, int d, int c)
+    {
+        const float4 *p = reinterpret_cast<const float4 *>(static_cast<const float *>(base) + id * d) + c;
+        return __ldg(p);
+    }
+};
+template <> struct Loader<__nv_bfloat16> {
+    static __device__ __forceinline__ float4 load(const void *base, int64_t id, int d, int c)
+    {
+        const uint2 *p = reinterpret_cast<const uint2 *>(static_cast<const uint16_t *>(base) + id * d) + c;
+        uint2 u = __ldg(p);
+        float4 f;
+        f.x = __uint_as_float(u.x << 16);
+        f.y = __uint_as_float(u.x & 0xFFFF0000u);
+        f.z = __uint_as_float(u.y << 16);
+        f.w = __uint_as_float(u.y & 0xFFFF0000u);
+        return f;
+    }
+};
+// e4m3 codes, 4 per 32-bit load; the per-dimension scale is applied by the caller
+template <> struct Loader<__nv_fp8_e4m3> {
+    static __device__ __forceinline__ float4 load(const void *base, int64_t id, int d, int c)
+    {
+        const unsigned *p = reinterpret_cast<const unsigned *>(static_cast<const uint8_t *>(base) + id * d) + c;
+        const unsigned u = __ldg(p);
+        const __half2 lo(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u & 0xFFFFu), __NV_E4M3));
+        const __half2 hi(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u >> 16), __NV_E4M3));
+        const float2 a = __half22float2(lo), b = __half22float2(hi);
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+};
+
+__device__ __forceinline__ float sqdiff4(float4 a, float4 b, float acc)
+{
+    float t = a.x - b.x;
+    acc = fmaf(t, t, acc);
+    t = a.y - b.y;
+    acc = fmaf(t, t, acc);
+    t = a.z - b.z;
+    acc = fmaf(t, t, acc);
+    t = a.w - b.w;
+    return fmaf(t, t, acc);
+}
+
+// Sums v[g] over the warp for G values at once (G a power of two <= 16): each
+// butterfly stage halves the values a lane holds by swapping halves with its
+// partner, then plain butterflies finish.  Afterwards every lane holds the full
+// sum of one value index; holder_lane<G>(g) names a lane holding value g.
+template <int G, int OFF> __device__ __forceinline__ void tr_stage(float (&v)[G], int lane, int held)
+{
+    const int half = held >> 1;
+    const bool hi = lane & OFF;
+#pragma unroll
+    for (int i = 0; i < G / 2; ++i) {
+        if (i < half) {
+            float send = hi ? v[i] : v[i + half];
+            float keep = hi ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(FULL, send, OFF);
+        }
+    }
+}
+
+template <int G> __device__ __forceinline__ float transpose_reduce(float (&v)[G], int lane)
+{
+    static_assert(G == 1 || G == 2 || G == 4 || G == 8 || G == 16, "G");
+    constexpr int m = log2i(G);
+    if constexpr (m >= 1)
+        tr_stage<G, 16>(v, lane, G);
+    if constexpr (m >= 2)
+        tr_stage<G, 8>(v, lane, G >> 1);
+    if constexpr (m >= 3)
+        tr_stage<G, 4>(v, lane, G >> 2);
+    if constexpr (m >= 4)
+        tr_stage<G, 2>(v, lane, G >> 3);
+    float s = v[0];
+#pragma unroll
+    for (int off = 16 >> m; off >= 1; off >>= 1)
+        s += __shfl_xor_sync(FULL, s, off);
+    return s;
+}
+
+template <int G> __device__ __forceinline__ int holder_lane(int g)
+{
+    constexpr int m = log2i(G);
+    int l = 0;
+#pragma unroll
+    for (int t = 0; t < m; ++t)
+        l |= ((g >> (m - 1 - t)) & 1) << (4 - t);
+    return l;
+}
+
+template <int V, class T, int HV, int KR> struct Warp {
+    // vectors per gather round: 16 loads in flight per lane at d <= 128
+    static constexpr int G0 = V >= 8 ? 2 : V >= 4 ? 4 : V >= 2 ? 8 : 16;
+    static constexpr int G = G0 < Tune<T>::gmax ? G0 : Tune<T>::gmax;
+    static constexpr int kOvf = Tune<T>::ovf;  // shared-memory overflow keys
+    static_assert(kOvf >= 64 && (kOvf & (kOvf - 1)) == 0, "the overflow holds a power of two >= 64 keys");
+    WarpSmem<HV, kOvf> &sm;
+    const SearchArgs &a;
+    const void *xs;  // vectors the search reads (float32 or bfloat16)
+    int lane;
+    unsigned *gbits;
+    int *glog;
+    u64 *gpool;
+    float4 qv[V];
+    float4 sv[V];  // e4m3 form: the per-dimension scales of this lane's coordinates
+    RegList<1> head;  // the nearest candidates, sorted
+    RegList<KR> res;
+    // per-query state, uniform across the warp
+    int nh, no, ng, cnt, ndc, nexp, nvis, nlog, kk, nscan, es;
+    int pf_node, pf_id;  // adjacency row already loaded for the next expansion
+    unsigned flags;
+    bool spill, rset, stop, padded, capped;
+    int seed_cnt, rins;  // probe features: seeds evaluated, result insertions
+    float seed_sum;
+    u64 seed1, seed2;
+    float r2;
+    u64 tau;  // every key in the global pool is >= tau (kMaxKey when it is empty)
+    double f2, bound2;
+
+    __device__ Warp(WarpSmem<HV, kOvf> &s, const SearchArgs &args, const void *x, int ln, unsigned *gb, int *gl, u64 *gp)
+        : sm(s), a(args), xs(x), lane(ln), gbits(gb), glog(gl), gpool(gp)
+    {
+    }
+
+    __device__ bool in_bound(u64 key) const { return (double)key_d2(key) <= bound2; }
+
+    // ---------------------------------------------------------------- visited set
+
+    // Test-and-set of one id by the calling lane; true if newly visited.
+    __device__ bool visit(int id)
+    {
+        unsigned h = hash_id(id) >> (32 - log2i(HV));
+        for (int t = 0; t < HV; ++t) {
+            int v = sm.vis[h];
+            if (v == id)
+                return false;
+            if (v == -1) {
+                if (spill)
+                    break;
+                int old = atomicCAS(&sm.vis[h], -1, id);
+                if (old == -1)
+                    return true;
+                if (old == id)
+                    return false;
+            }
+            h = (h + 1) & (HV - 1);
+        }
+        const unsigned bit = 1u << (id & 31);
+        return (atomicOr(&gbits[id >> 5], bit) & bit) == 0;
+    }
+
+    // Past half load of the shared table, new ids go to the bitmap.
+    __device__ void begin_batch()
+    {
+        if (!spill && nvis >= HV / 2 - 32)
+            spill = true;
+    }
+
+    // Leaves the bitmap all zero for the next query: clears the logged words,
+    // or the whole bitmap if the log overflowed.
+    __device__ void clear_bits()
+    {
+        if (!spill)
+            return;
+        if (nlog <= kVisitLog) {
+            for (int i = lane; i < nlog; i += 32)
+                gbits[glog[i] >> 5] = 0u;
+        } else {
+            for (int64_t i = lane; i < a.bits_words; i += 32)
+                gbits[i] = 0u;
+        }
+        __syncwarp();
+    }
+
+    // ---------------------------------------------------------------- distances
+
+    // Squared distances of the ids held by the lanes in `mask`; returns this lane's.
+    template <class L> __device__ float distances(const void *base, int id, unsigned mask)
+    {
+        float mine = 0.0f;
+        const int chunks = a.d >> 2;
+        while (mask) {
+            // slot g takes the g-th id of the mask; every slot loads (empty slots
+            // read row 0 and are masked), so all loads issue back to back
+            int src[G];
+            int gid[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                src[g] = mask ? __ffs(mask) - 1 : -1;
+                mask &= mask - 1;
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const int sid = __shfl_sync(FULL, id, src[g] < 0 ? 0 : src[g]);
+                gid[g] = (src[g] < 0 || sid < 0) ? 0 : sid;
+            }
+            float4 xv[G][V];
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const int c = lane + 32 * v;
+                    xv[g][v] = L::load(base, gid[g], a.d, c < chunks ? c : 0);
+                    if constexpr (std::is_same<L, Loader<__nv_fp8_e4m3>>::value) {
+                        // dequantise with a rounded product (never fused into the difference)
+                        xv[g][v] = make_float4(__fmul_rn(sv[v].x, xv[g][v].x), __fmul_rn(sv[v].y, xv[g][v].y),
+                                               __fmul_rn(sv[v].z, xv[g][v].z), __fmul_rn(sv[v].w, xv[g][v].w));
+                    }
+                }
+            float acc[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                acc[g] = 0.0f;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    int c = lane + 32 * v;
+                    if (src[g] >= 0 && c < chunks)
+                        acc[g] = sqdiff4(qv[v], xv[g][v], acc[g]);
+                }
+            }
+            float red = transpose_reduce<G>(acc, lane);
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                float s = __shfl_sync(FULL, red, holder_lane<G>(g));
+                if (lane == src[g])
+                    mine = s;
+            }
+        }
+        return mine;
+    }
+
+    // ---------------------------------------------------------------- result list
+
+    // Inserts key into R; false if R keeps its k entries (key would be evicted).
+    __device__ bool r_insert(u64 key)
+    {
+        const int pos = res.rank(key);
+        if (pos >= kk)
+            return false;
+        res.insert_at(pos, key, lane, kk);
+        cnt = min(cnt + 1, kk);
+        return true;
+    }
+
+    __device__ void update_bound() { bound2 = (rset && !isinf(f2)) ? (double)r2 * f2 : INFINITY; }
+
+    // ---------------------------------------------------------------- candidate pool
+
+    // Appends the keys of the lanes with `put` to the global pool.
+    __device__ void gpool_append(bool put, u64 key)
+    {
+        unsigned m = __ballot_sync(FULL, put);
+        if (!m)
+            return;
+        if (put) {
+            int dst = ng + __popc(m & lanemask_lt(lane));
+            if (dst < kGlobalPool)
+                gpool[dst] = key;
+        }
+        if (ng + __popc(m) > kGlobalPool)
+            flags |= ONNG_FLAG_S_OVERFLOW;
+        ng = min(ng + __popc(m), kGlobalPool);
+    }
+
+    // Makes room for `need` (<= 32) more keys in the overflow: drops its
+    // out-of-bound keys; if they still do not fit, sorts it and moves the
+    // farther half to the global pool (so at most kOvf / 2 keys remain).
+    __device__ void make_room(int need)
+    {
+        int w = 0;
+        for (int base = 0; base < no; base += 32) {
+            const int e = base + lane;
+            const u64 kv = e < no ? sm.ovf[e] : kMaxKey;
+            const bool keep = e < no && in_bound(kv);
+            const unsigned km = __ballot_sync(FULL, keep);
+            __syncwarp();
+            if (keep)
+                sm.ovf[w + __popc(km & lanemask_lt(lane))] = kv;
+            w += __popc(km);
+            __syncwarp();
+        }
+        no = w;
+        if (no + need <= kOvf)
+            return;
+        // no > kOvf - need >= kOvf / 2, so the element at kOvf / 2 is a real key
+        constexpr int N = kOvf / 32;
+        u64 v[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            v[i] = i * 32 + lane < no ? sm.ovf[i * 32 + lane] : kMaxKey;
+        warp_bitonic_sort<N>(v, lane);
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i)
+            sm.ovf[i * 32 + lane] = v[i];
+        const u64 first_moved = __shfl_sync(FULL, v[N / 2], 0);
+#pragma unroll
+        for (int i = N / 2; i < N; ++i)
+            gpool_append(v[i] != kMaxKey, v[i]);
+        __syncwarp();
+        tau = first_moved;
+        no = kOvf / 2;
+    }
+
+    __device__ void ovf_append(u64 key)
+    {
+        if (no == kOvf)
+            make_room(1);
+        if (key >= tau) {
+            gpool_append(lane == 0, key);
+            return;
+        }
+        if (lane == 0)
+            sm.ovf[no] = key;
+        ++no;
+        __syncwarp();
+    }
+
+    // Refills the empty overflow with the 64 nearest in-bound global keys.
+    __device__ void refill_ovf()
+    {
+        u64 v[8];  // v[0..1]: best 64 so far; v[2..5]: next 128 global keys
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            v[i] = kMaxKey;
+        for (int base = 0; base < ng; base += 128) {
+#pragma unroll
+            for (int i = 2; i < 6; ++i) {
+                int e = base + (i - 2) * 32 + lane;
+                u64 kv = e < ng ? gpool[e] : kMaxKey;
+                v[i] = (kv != kMaxKey && in_bound(kv)) ? kv : kMaxKey;
+            }
+            v[6] = v[7] = kMaxKey;
+            warp_bitonic_sort<8>(v, lane);
+        }
+        const u64 kth = __shfl_sync(FULL, v[1], 31);
+        sm.ovf[lane] = v[0];
+        sm.ovf[32 + lane] = v[1];
+        no = __popc(__ballot_sync(FULL, v[0] != kMaxKey)) + __popc(__ballot_sync(FULL, v[1] != kMaxKey));
+        // keep the global entries beyond kth that are still in bound
+        int w = 0;
+        u64 mn = kMaxKey;
+        for (int base = 0; base < ng; base += 32) {
+            int e = base + lane;
+            u64 kv = e < ng ? gpool[e] : kMaxKey;
+            bool keep = e < ng && kv > kth && in_bound(kv);
+            unsigned km = __ballot_sync(FULL, keep);
+            __syncwarp();
+            if (keep) {
+                gpool[w + __popc(km & lanemask_lt(lane))] = kv;
+                mn = kv < mn ? kv : mn;
+            }
+            w += __popc(km);
+            __syncwarp();
+        }
+        ng = w;
+        tau = warp_min_u64(mn);
+        __syncwarp();
+    }
+
+    // Refills the empty head with the 32 nearest in-bound overflow keys.
+    __device__ void refill_head()
+    {
+        if (no == 0) {
+            if (ng == 0)
+                return;
+            refill_ovf();
+        }
+        constexpr int N = kOvf / 32;
+        u64 v[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const int e = i * 32 + lane;
+            const u64 kv = e < no ? sm.ovf[e] : kMaxKey;
+            v[i] = (kv != kMaxKey && in_bound(kv)) ? kv : kMaxKey;
+        }
+        warp_bitonic_sort<N>(v, lane);
+        head.v[0] = v[0];
+        nh = __popc(__ballot_sync(FULL, v[0] != kMaxKey));
+        int m = 0;
+#pragma unroll
+        for (int i = 1; i < N; ++i)
+            m += __popc(__ballot_sync(FULL, v[i] != kMaxKey));
+        __syncwarp();
+#pragma unroll
+        for (int i = 1; i < N; ++i)
+            if ((i - 1) * 32 + lane < m)
+                sm.ovf[(i - 1) * 32 + lane] = v[i];
+        no = m;
+        __syncwarp();
+    }
+
+    // Appends the keys of the lanes with `put` (all < tau) to the shared overflow,
+    // making room first if they do not fit; keys that end up >= tau after that
+    // go to the global pool.
+    __device__ void ovf_append_many(bool put, u64 key)
+    {
+        unsigned m = __ballot_sync(FULL, put);
+        if (!m)
+            return;
+        if (no + __popc(m) > kOvf) {
+            make_room(__popc(m));  // tau may drop
+            const bool far = put && key >= tau;
+            gpool_append(far, key);
+            put = put && !far;
+            m = __ballot_sync(FULL, put);
+        }
+        if (put)
+            sm.ovf[no + __popc(m & lanemask_lt(lane))] = key;
+        no += __popc(m);
+        __syncwarp();
+    }
+
+    // Adds the batch members marked `push` to S.  Keys >= tau go to the global
+    // pool and keys >= the head's maximum to the overflow, each in one step;
+    // only keys that enter the sorted head are inserted one at a time.  While S
+    // is the head alone (no overflow, empty pool) every key is inserted in turn.
+    __device__ void pool_push(bool push, u64 key)
+    {
+        unsigned pm = __ballot_sync(FULL, push);
+        if (!pm)
+            return;
+        if (no > 0 || ng > 0) {
+            const bool far = push && key >= tau;
+            gpool_append(far, key);
+            push = push && !far;
+            const u64 hmax = nh > 0 ? __shfl_sync(FULL, head.v[0], nh - 1) : kMaxKey;
+            const bool to_ovf = push && key >= hmax;
+            ovf_append_many(to_ovf, key);
+            push = push && !to_ovf;
+            pm = __ballot_sync(FULL, push);
+        }
+        while (pm) {
+            const int src = __ffs(pm) - 1;
+            pm &= pm - 1;
+            const u64 ck = __shfl_sync(FULL, key, src);
+            if (ck >= tau) {
+                gpool_append(lane == 0, ck);
+                continue;
+            }
+            const u64 hmax = nh > 0 ? __shfl_sync(FULL, head.v[0], nh - 1) : kMaxKey;
+            const bool only_head = no == 0 && ng == 0;
+            if (ck < hmax || (only_head && nh < 32)) {
+                if (nh == 32)
+                    ovf_append(hmax);  // the evicted maximum stays >= the rest of the head
+                head.insert_at(head.rank(ck), ck, lane, 32);
+                nh = min(nh + 1, 32);
+            } else {
+                ovf_append(ck);
+            }
+        }
+    }
+
+    // Removes and returns the minimum of S (the head's first key); refills the
+    // head when it runs empty.
+    __device__ u64 pool_pop()
+    {
+        const u64 top = __shfl_sync(FULL, head.v[0], 0);
+        head.pop_front(lane);
+        --nh;
+        if (nh == 0 && (no > 0 || ng > 0))
+            refill_head();
+        return top;
+    }
+
+    // ---------------------------------------------------------------- one batch
+
+    // Tests a batch of up to 32 ids (one per lane, -1 = none) and applies it.
+    // With `predict`, loads the adjacency row of the node expanded next.
+    __device__ void batch(int id, bool init, bool predict)
+    {
+        begin_batch();
+        bool isnew = id >= 0 && visit(id);
+        unsigned mask = __ballot_sync(FULL, isnew);
+        if (!mask)
+            return;
+        int nnew = __popc(mask);
+        ndc += nnew;
+        if (spill) {
+            const int pos = nlog + __popc(mask & lanemask_lt(lane));
+            if (isnew && pos < kVisitLog)
+                glog[pos] = id;
+            nlog += nnew;
+        } else {
+            nvis += nnew;
+        }
+        __syncwarp();
+        float d2 = distances<Loader<T>>(xs, id, mask);
+        u64 key = pack_key(d2, id);
+        if (init && a.feat) {
+            float sd = isnew ? sqrtf(d2) : 0.f;
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1)
+                sd += __shfl_xor_sync(FULL, sd, off);
+            seed_sum += sd;
+            seed_cnt += nnew;
+        }
+        if (predict) {
+            // next pop = min(S head, nearest batch member if it is pushed)
+            const u64 bmin = warp_min_u64(isnew ? key : kMaxKey);
+            const u64 top = __shfl_sync(FULL, head.v[0], 0);
+            const u64 next = ((double)key_d2(bmin) <= bound2 && bmin < top) ? bmin : top;
+            if (next != kMaxKey) {
+                pf_node = key_id(next);
+                pf_id = lane < es ? a.adj[(int64_t)pf_node * a.adj_w + lane] : -1;
+            }
+        }
+        // R <- the best kk of R and the batch
+        unsigned cm = __ballot_sync(FULL, isnew && (init || !rset || d2 <= r2));
+        while (cm) {
+            int src = __ffs(cm) - 1;
+            cm &= cm - 1;
+            u64 ck = __shfl_sync(FULL, key, src);
+            if (init || !rset || key_d2(ck) <= r2) {
+                if (r_insert(ck) && !init)
+                    ++rins;
+                if (!init && cnt == kk) {
+                    rset = true;
+                    r2 = key_d2(res.get(kk - 1));
+                }
+            }
+        }
+        update_bound();
+        // S <- S + batch members within r(1+eps)
+        pool_push(isnew && (double)d2 <= bound2, key);
+    }
+
+    __device__ void run(int64_t q)
+    {
+        const int d = a.d;
+        const float *qp = a.Q + q * d;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            int c = lane + 32 * v;
+            qv[v] = c < (d >> 2) ? __ldg(reinterpret_cast<const float4 *>(qp) + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (std::is_same<T, __nv_fp8_e4m3>::value)
+                sv[v] = c < (d >> 2) ? __ldg(reinterpret_cast<const float4 *>(a.scale8) + c)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const float eps = a.eps_q ? a.eps_q[q] : a.eps;
+        es = a.es_q ? a.es_q[q] : a.e_s;
+        if (es <= 0)
+            es = INT_MAX;
+        padded = a.adj != nullptr && es <= a.adj_w;
+        const bool predict = padded && es <= 32;
+        f2 = isinf(eps) ? INFINITY : (1.0 + (double)eps) * (1.0 + (double)eps);
+        for (int i = lane; i < HV; i += 32)
+            sm.vis[i] = -1;
+        head.clear();
+        res.clear();
+        nh = no = ng = cnt = ndc = nexp = nvis = nlog = nscan = 0;
+        pf_node = -1;
+        kk = a.k;
+        flags = 0;
+        spill = rset = stop = capped = false;
+        seed_cnt = rins = 0;
+        seed_sum = 0.f;
+        r2 = INFINITY;
+        tau = kMaxKey;
+        bound2 = INFINITY;
+        __syncwarp();
+        for (int c0 = 0; c0 < a.n_seed; c0 += 32) {
+            int id = -1;
+            if (c0 + lane < a.n_seed) {
+                id = a.seeds[q * a.n_seed + c0 + lane];
+                if (id >= a.n)
+                    id = -1;
+            }
+            batch(id < 0 ? -1 : id, true, false);
+        }
+        seed1 = head.get(0);
+        seed2 = head.get(1);
+        while (!stop) {
+            if (nh == 0) {
+                refill_head();
+                if (nh == 0)
+                    break;
+            }
+            if (a.max_exp > 0 && nexp >= a.max_exp) {
+                // capped with a candidate still to expand (not merely pending termination)
+                capped = (double)key_d2(__shfl_sync(FULL, head.v[0], 0)) <= bound2;
+                if (capped)
+                    flags |= ONNG_FLAG_LIMIT;
+                break;
+            }
+            const u64 sk = pool_pop();
+            if ((double)key_d2(sk) > bound2)
+                break;
+            ++nexp;
+            const int s = key_id(sk);
+            if (predict) {
+                const int id = s == pf_node ? pf_id : (lane < es ? a.adj[(int64_t)s * a.adj_w + lane] : -1);
+                pf_node = -1;
+                nscan += __popc(__ballot_sync(FULL, id >= 0));
+                batch(id, false, true);
+            } else if (padded) {
+                for (int c0 = 0; c0 < es && !stop; c0 += 32) {
+                    const int id = c0 + lane < es ? a.adj[(int64_t)s * a.adj_w + c0 + lane] : -1;
+                    const unsigned got = __ballot_sync(FULL, id >= 0);
+                    if (!got)
+                        break;
+                    nscan += __popc(got);
+                    batch(id, false, false);
+                }
+            } else {
+                const int64_t beg = a.row_ptr[s];
+                const int64_t deg = a.row_ptr[s + 1] - beg;
+                const int m = deg < (int64_t)es ? (int)deg : es;
+                nscan += m;
+                for (int c0 = 0; c0 < m && !stop; c0 += 32) {
+                    int id = c0 + lane < m ? a.col[beg + c0 + lane] : -1;
+                    batch(id, false, false);
+                }
+            }
+        }
+    }
+
+    // Rescores the kept list in float32 against X and keeps the best k_out.
+    __device__ void rerank()
+    {
+        u64 nk[KR];
+#pragma unroll
+        for (int i = 0; i < KR; ++i) {
+            const int id = res.v[i] == kMaxKey ? -1 : key_id(res.v[i]);
+            const unsigned mask = __ballot_sync(FULL, id >= 0);
+            const float dv = distances<Loader<float>>(a.X, id, mask);
+            nk[i] = id >= 0 ? pack_key(dv, id) : kMaxKey;
+        }
+        res.clear();
+        cnt = 0;
+        kk = a.k_out;
+#pragma unroll
+        for (int i = 0; i < KR; ++i) {
+            unsigned m = __ballot_sync(FULL, nk[i] != kMaxKey);
+            while (m) {
+                const int src = __ffs(m) - 1;
+                m &= m - 1;
+                r_insert(__shfl_sync(FULL, nk[i], src));
+            }
+        }
+    }
+
+    // Probe features after the capped search (all logs natural, distances Euclidean).
+    __device__ void features(int64_t q)
+    {
+        const u64 rbk = res.get(0);
+        const u64 rkk = res.get(cnt > 0 ? cnt - 1 : 0);
+        const u64 hk = __shfl_sync(FULL, head.v[0], 0);
+        if (lane != 0)
+            return;
+        const float e6 = 1e-6f;
+        const float ds1 = seed1 == kMaxKey ? 0.f : sqrtf(key_d2(seed1));
+        const float ds2 = seed2 == kMaxKey ? ds1 : sqrtf(key_d2(seed2));
+        const float dmean = seed_cnt > 0 ? seed_sum / (float)seed_cnt : ds1;
+        const float rb = cnt > 0 ? sqrtf(key_d2(rbk)) : ds1;
+        const float rk = cnt > 0 ? sqrtf(key_d2(rkk)) : ds1;
+        const float bound = (rset && !isinf(f2)) ? (float)sqrt(bound2) : INFINITY;
+        float top = capped ? fminf(sqrtf(key_d2(hk)), bound) : bound;
+        if (isinf(top))
+            top = rk;
+        float *f = a.feat + q * kFeat;
+        f[0] = a.target;
+        f[1] = logf(ds1 + e6);
+        f[2] = logf((ds2 + e6) / (ds1 + e6));
+        f[3] = logf((dmean + e6) / (ds1 + e6));
+        f[4] = logf((rb + e6) / (ds1 + e6));
+        f[5] = logf((rk + e6) / (rb + e6));
+        f[6] = logf((top + e6) / (rb + e6));
+        f[7] = (float)ndc / (float)max(1, seed_cnt + nscan);
+        f[8] = (float)nexp / (float)max(1, a.max_exp);
+        f[9] = log1pf((float)ndc);
+        f[10] = (float)rins / (float)max(1, ndc);
+        f[11] = rset ? 1.f : 0.f;
+        f[12] = logf((rk + e6) / (ds1 + e6));
+        f[13] = log1pf((float)nscan);
+        f[14] = capped ? 1.f : 0.f;
+        f[15] = logf((float)a.d) / 8.f;
+    }
+
+    __device__ void write(int64_t q)
+    {
+        if (a.feat)
+            features(q);
+        const int k = a.k_out;
+#pragma unroll
+        for (int i = 0; i < KR; ++i) {
+            const int e = i * 32 + lane;
+            if (e < k && a.out_ids) {
+                a.out_ids[q * k + e] = e < cnt ? key_id(res.v[i]) : -1;
+                a.out_dist[q * k + e] = e < cnt ? sqrtf(key_d2(res.v[i])) : INFINITY;
+            }
+        }
+        if (a.stats && lane == 0) {
+            a.stats[q * 4 + 0] = ndc;
+            a.stats[q * 4 + 1] = nexp;
+            a.stats[q * 4 + 2] = nscan;
+            a.stats[q * 4 + 3] = (int)flags;
+        }
+    }
+};
+
+// Resident CTAs per SM the register budget is sized for (a few spilled bytes at
+// most).  Shared memory holds 5 CTAs of float32 warps (2048-slot table and 256
+// overflow keys each) or 6 of bfloat16 warps (128 overflow keys).
+template <class T> __host__ __device__ constexpr int min_blocks(int V, int KR)
+{
+    return V <= 2 && KR == 1 ? Tune<T>::minb : 3;
+}
+
+template <int V, class T, int HV, int KR>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, min_blocks<T>(V, KR)) search_kernel(SearchArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto *smem = reinterpret_cast<WarpSmem<HV, Tune<T>::ovf> *>(smem_raw);
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t slot = (int64_t)blockIdx.x * kWarpsPerCta + warp;
+    const void *xs = std::is_same<T, float>::value           ? static_cast<const void *>(a.X)
+                     : std::is_same<T, __nv_bfloat16>::value ? static_cast<const void *>(a.Xb)
+                                                              : static_cast<const void *>(a.X8);
+    Warp<V, T, HV, KR> w(smem[warp], a, xs, lane, a.gbits + slot * a.bits_words, a.glog + slot * kVisitLog,
+                         a.gpool + slot * kGlobalPool);
+    for (;;) {
+        int q = 0;
+        if (lane == 0)
+            q = atomicAdd(a.counter, 1);
+        q = __shfl_sync(FULL, q, 0);
+        if (q >= a.nq)
+            break;
+        w.run(q);
+        w.clear_bits();
+        if constexpr (!std::is_same<T, float>::value)
+            w.rerank();
+        w.write(q);
+        __syncwarp();
+    }
+}
+
+struct Launch {
+    void (*fn)(SearchArgs);
+    size_t smem;
+};
+
+// The search kernel for vector type T with V float4 chunks per lane (d <= 128 V)
+// and a kept list of at most 32 KR keys (KR = 1 or kMaxK / 32); defined in
+// search_inst.cu.
+template <class T, int V, int KR> Launch pick();
+#define ONNG_SEARCH_DECLARE_PICK(T, V)   \
+    template <> Launch pick<T, V, 1>(); \
+    template <> Launch pick<T, V, kMaxK / 32>();
+#define ONNG_SEARCH_DECLARE_PICKS(T)    \
+    ONNG_SEARCH_DECLARE_PICK(T, 1)      \
+    ONNG_SEARCH_DECLARE_PICK(T, 2)      \
+    ONNG_SEARCH_DECLARE_PICK(T, 4)      \
+    ONNG_SEARCH_DECLARE_PICK(T, 8)
+ONNG_SEARCH_DECLARE_PICKS(float)
+ONNG_SEARCH_DECLARE_PICKS(__nv_bfloat16)
+ONNG_SEARCH_DECLARE_PICKS(__nv_fp8_e4m3)
+#undef ONNG_SEARCH_DECLARE_PICKS
+#undef ONNG_SEARCH_DECLARE_PICK
+
+}  // namespace sk
+}  // namespace onng
