@@ -42,7 +42,7 @@ enum onng_status {
 };
 
 /* per-query flags, stats[q*4 + 3] */
-#define ONNG_FLAG_S_OVERFLOW 1u      /* candidate pool full: farthest candidates dropped */
+#define ONNG_FLAG_S_OVERFLOW 1u      /* candidate spill pool full: candidates dropped (see pool_cap) */
 #define ONNG_FLAG_VISIT_OVERFLOW 2u  /* reserved (the visited set cannot overflow) */
 #define ONNG_FLAG_LIMIT 4u           /* stopped by max_expansions with an in-bound candidate left */
 
@@ -173,6 +173,11 @@ typedef struct {
     int32_t precision;
     int32_t k_rerank;        /* bf16 only: candidates rescored in float32 (>= k) */
     int32_t max_expansions;  /* 0: no cap; else per-query cap -> ONNG_FLAG_LIMIT */
+    int32_t pool_cap;        /* candidate spill-pool entries per warp (0: 16384).  A query
+                                whose candidates outgrow the pool drops the ones that
+                                arrive when it is full (each farther than every
+                                candidate kept outside the pool) and is flagged
+                                ONNG_FLAG_S_OVERFLOW; larger pools take more workspace */
 } onng_search_params;
 
 size_t onng_search_workspace_bytes(int64_t nq, const onng_index *idx, const onng_search_params *p);
@@ -216,7 +221,9 @@ int onng_search_probe(const onng_index *idx, const float *Q, int64_t nq, const o
  *
  * The first call on a device looks up the array's device address (with that
  * device current) and keeps it; make that first call before any stream
- * capture.  Every call clears the parts that must start at zero (the query
+ * capture.  The kept address belongs to the device's primary context: after
+ * cudaDeviceReset (or anything else that tears that context down) do not call
+ * this entry point again in the same process.  Every call clears the parts that must start at zero (the query
  * counter and the bitmaps) on its stream, so a call sees nothing of the
  * previous one.  All calls on a device share the one array: calls whose
  * kernels can overlap on the GPU (other streams, other host threads) race

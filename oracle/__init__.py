@@ -67,6 +67,9 @@ def _load():
             lib.oracle_search.argtypes = [vp, vp, vp, i64, i32, vp, i64, i32, i32, dbl, vp, i32,
                                           vp, vp, vp, i32]
             lib.oracle_search.restype = i32
+            lib.oracle_search_margin.argtypes = [vp, vp, vp, i64, i32, vp, i64, i32, i32, dbl, vp, i32,
+                                                 vp, vp, vp, vp, i32]
+            lib.oracle_search_margin.restype = i32
             lib.oracle_search_probe.argtypes = [vp, vp, vp, i64, i32, vp, i64, i32, i32, dbl, vp, i32,
                                                 i64, dbl, vp, vp, i32]
             lib.oracle_search_probe.restype = i32
@@ -234,8 +237,13 @@ def hash_selftest(ids, n: int):
     return out.astype(bool)
 
 
-def search(ptr, col, X, Q, k: int, e_s: int, eps: float, seeds, threads: int = 0):
-    """Algorithm 1 for every query.  Returns (ids int32, dist float64, stats int64 [nq,4])."""
+def search(ptr, col, X, Q, k: int, e_s: int, eps: float, seeds, threads: int = 0, margin: bool = False):
+    """Algorithm 1 for every query.  Returns (ids int32, dist float64, stats int64 [nq,4]).
+
+    With ``margin`` also returns, per query, the smallest relative gap of any
+    comparison the run decided (float64 [nq]; inf when it compared nothing): a
+    run whose margin exceeds another arithmetic's relative rounding error takes
+    every decision the same way in that arithmetic."""
     ptr = _c(ptr, np.int64)
     col = _c(col, np.int32)
     X = _c(X, np.float32)
@@ -246,6 +254,13 @@ def search(ptr, col, X, Q, k: int, e_s: int, eps: float, seeds, threads: int = 0
     ids = np.empty((nq, k), np.int32)
     dist = np.empty((nq, k), np.float64)
     stats = np.empty((nq, 4), np.int64)
+    if margin:
+        mg = np.empty(nq, np.float64)
+        rc = _load().oracle_search_margin(_p(ptr), _p(col), _p(X), n, d, _p(Q), nq, k, e_s, float(eps),
+                                          _p(seeds), seeds.shape[1], _p(ids), _p(dist), _p(stats), _p(mg),
+                                          threads)
+        assert rc == 0, rc
+        return ids, dist, stats, mg
     rc = _load().oracle_search(_p(ptr), _p(col), _p(X), n, d, _p(Q), nq, k, e_s, float(eps),
                                _p(seeds), seeds.shape[1], _p(ids), _p(dist), _p(stats), threads)
     assert rc == 0, rc

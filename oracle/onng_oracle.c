@@ -21,6 +21,9 @@
  *   oracle_adjust_path_alg4  Algorithm 4 taken literally (round-robin, ascending ids)
  *   oracle_search         KnnSearch, Algorithm 1, with the visited set of
  *                         Algorithms Set/IsSet (Sec. 2.5) and e_p of Eq. 1 as e_s
+ *   oracle_search_margin  the same search, also returning per query the smallest
+ *                         relative gap of any comparison it decided (a test aid:
+ *                         how close the run came to a tie)
  *   oracle_search_probe   Algorithm 1 stopped after h expansions, with the features
  *                         the learned (eps, e_s) predictor reads (no paper counterpart)
  *   oracle_seeds_random   random seed rule (the paper's "rand" seeds, Sec. 3)
@@ -702,6 +705,34 @@ typedef struct {
     int32_t id;
 } cand_t;
 
+/* Folds the comparison of a with b into *mg, the smallest relative gap
+ * |a - b| / max(|a|, |b|) seen so far (0 for an exact tie). */
+static void near_gap(double *mg, double a, double b)
+{
+    double m = fabs(a) > fabs(b) ? fabs(a) : fabs(b);
+    double g = m > 0.0 ? fabs(a - b) / m : 0.0;
+    if (g < *mg)
+        *mg = g;
+}
+
+/* Index of the largest entry of R[0..nr) by (distance, id); the gap between it
+ * and the second largest is folded into *mg when mg is not NULL. */
+static int64_t argmax_r(const cand_t *R, int64_t nr, double *mg)
+{
+    int64_t b = 0;
+    for (int64_t u = 1; u < nr; ++u)
+        if (lt_pair(R[b].d, R[b].id, R[u].d, R[u].id))
+            b = u;
+    if (mg && nr >= 2) {
+        int64_t c = b == 0 ? 1 : 0;
+        for (int64_t u = 0; u < nr; ++u)
+            if (u != b && lt_pair(R[c].d, R[c].id, R[u].d, R[u].id))
+                c = u;
+        near_gap(mg, R[b].d, R[c].d);
+    }
+    return b;
+}
+
 int oracle_hash_selftest(const int32_t *ids, int64_t m, int64_t n, uint8_t *was_set)
 {
     visited_t v;
@@ -730,11 +761,21 @@ int oracle_hash_selftest(const int32_t *ids, int64_t m, int64_t n, uint8_t *was_
  * Output rows: R ordered by (distance, id), padded with -1 / +inf.
  * stats [nq, 4]: distance computations, expansions (nodes popped and scanned),
  * largest |S|, flags (0).
+ *
+ * margin [nq] (optional): the smallest relative gap |a - b| / max(a, b) over the
+ * comparisons this run decided: the popped s against the runner-up of S, s
+ * against r(1 + eps) when testing termination, every new distance against
+ * r(1 + eps) (entry to S) and against r (entry to R), and the evicted element of
+ * R against the runner-up.  A popped s that is itself the element defining r is
+ * not compared with r (eps = 0): both sides see the same value there.  A run
+ * whose margin exceeds the relative rounding error of another arithmetic takes
+ * every decision the same way in that arithmetic, so its results and counts
+ * are the same; a smaller margin marks a query where a near-tie may go either way.
  */
 static int search_core(const int64_t *ptr, const int32_t *col, const float *X, int64_t n, int d,
                        const float *Q, int64_t nq, int k, int e_s, double eps, const int32_t *seeds,
                        int n_seed, int32_t *out_ids, double *out_dist, int64_t *stats, int threads,
-                       int64_t max_exp, double target, double *feat)
+                       int64_t max_exp, double target, double *feat, double *margin)
 {
     if (k <= 0 || d <= 0 || n <= 0 || n_seed <= 0)
         return ORACLE_E_INVAL;
@@ -767,6 +808,9 @@ static int search_core(const int64_t *ptr, const int32_t *col, const float *X, i
             visited_clear(&vis);
             int64_t ns = 0, nr = 0, maxs = 0, ndc = 0, nexp = 0, nscan = 0, rins = 0, nseed = 0;
             double r = INFINITY, seed_sum = 0.0;
+            int32_t r_id = -1; /* the element of R whose distance is r */
+            double mg = INFINITY;
+            double *mgp = margin ? &mg : NULL;
             int capped = 0;
             /* S <- Seed(G), R <- S (k nearest), C <- seeds */
             for (int t = 0; t < n_seed; ++t) {
@@ -799,10 +843,7 @@ static int search_core(const int64_t *ptr, const int32_t *col, const float *X, i
                 /* R keeps the k nearest seeds: insert, evict the largest when |R| > k */
                 R[nr++] = S[t];
                 if (nr > k) {
-                    int64_t a = 0;
-                    for (int64_t u = 1; u < nr; ++u)
-                        if (lt_pair(R[a].d, R[a].id, R[u].d, R[u].id))
-                            a = u;
+                    int64_t a = argmax_r(R, nr, mgp);
                     R[a] = R[--nr];
                 }
             }
@@ -812,6 +853,13 @@ static int search_core(const int64_t *ptr, const int32_t *col, const float *X, i
                 for (int64_t u = 1; u < ns; ++u)
                     if (lt_pair(S[u].d, S[u].id, S[a].d, S[a].id))
                         a = u;
+                if (mgp && ns >= 2) {
+                    int64_t c = a == 0 ? 1 : 0;
+                    for (int64_t u = 0; u < ns; ++u)
+                        if (u != a && lt_pair(S[u].d, S[u].id, S[c].d, S[c].id))
+                            c = u;
+                    near_gap(mgp, S[a].d, S[c].d);
+                }
                 double bound = isinf(eps) ? INFINITY : r * (1.0 + eps);
                 if (max_exp > 0 && nexp >= max_exp) { /* probe: stop after max_exp hops */
                     capped = S[a].d <= bound;
@@ -819,6 +867,8 @@ static int search_core(const int64_t *ptr, const int32_t *col, const float *X, i
                 }
                 cand_t s = S[a];
                 S[a] = S[--ns];
+                if (mgp && !isinf(bound) && !(eps == 0.0 && s.id == r_id))
+                    near_gap(mgp, s.d, bound);
                 if (s.d > bound)
                     break;
                 ++nexp;
@@ -832,6 +882,10 @@ static int search_core(const int64_t *ptr, const int32_t *col, const float *X, i
                     double dn = dist64(q, X + (int64_t)nb * d, d);
                     ++ndc;
                     bound = isinf(eps) ? INFINITY : r * (1.0 + eps);
+                    if (mgp && !isinf(bound))
+                        near_gap(mgp, dn, bound);
+                    if (mgp && !isinf(r))
+                        near_gap(mgp, dn, r);
                     if (dn <= bound) {
                         if (ns == scap) {
                             scap *= 2;
@@ -849,19 +903,15 @@ static int search_core(const int64_t *ptr, const int32_t *col, const float *X, i
                         ++nr;
                         int survived = 1;
                         if (nr > k) {
-                            int64_t b = 0;
-                            for (int64_t u = 1; u < nr; ++u)
-                                if (lt_pair(R[b].d, R[b].id, R[u].d, R[u].id))
-                                    b = u;
+                            int64_t b = argmax_r(R, nr, mgp);
                             survived = b != nr - 1;
                             R[b] = R[--nr];
                         }
                         rins += survived;
                         if (nr == k) {
-                            r = R[0].d;
-                            for (int64_t u = 1; u < nr; ++u)
-                                if (R[u].d > r)
-                                    r = R[u].d;
+                            int64_t b = argmax_r(R, nr, NULL);
+                            r = R[b].d;
+                            r_id = R[b].id;
                         }
                     }
                 }
@@ -880,6 +930,8 @@ static int search_core(const int64_t *ptr, const int32_t *col, const float *X, i
                 out_ids[qi * k + t] = t < nr ? R[t].id : -1;
                 out_dist[qi * k + t] = t < nr ? R[t].d : INFINITY;
             }
+            if (margin)
+                margin[qi] = mg;
             if (stats) {
                 stats[qi * 4 + 0] = ndc;
                 stats[qi * 4 + 1] = nexp;
@@ -933,7 +985,16 @@ int oracle_search(const int64_t *ptr, const int32_t *col, const float *X, int64_
                   int n_seed, int32_t *out_ids, double *out_dist, int64_t *stats, int threads)
 {
     return search_core(ptr, col, X, n, d, Q, nq, k, e_s, eps, seeds, n_seed, out_ids, out_dist,
-                       stats, threads, 0, 0.0, NULL);
+                       stats, threads, 0, 0.0, NULL, NULL);
+}
+
+int oracle_search_margin(const int64_t *ptr, const int32_t *col, const float *X, int64_t n, int d,
+                         const float *Q, int64_t nq, int k, int e_s, double eps, const int32_t *seeds,
+                         int n_seed, int32_t *out_ids, double *out_dist, int64_t *stats, double *margin,
+                         int threads)
+{
+    return search_core(ptr, col, X, n, d, Q, nq, k, e_s, eps, seeds, n_seed, out_ids, out_dist,
+                       stats, threads, 0, 0.0, NULL, margin);
 }
 
 /*
@@ -952,7 +1013,7 @@ int oracle_search_probe(const int64_t *ptr, const int32_t *col, const float *X, 
     int32_t *ids = (int32_t *)malloc((size_t)(nq > 0 ? nq : 1) * (size_t)k * sizeof(int32_t));
     double *dist = (double *)malloc((size_t)(nq > 0 ? nq : 1) * (size_t)k * sizeof(double));
     int rc = search_core(ptr, col, X, n, d, Q, nq, k, e_s, eps, seeds, n_seed, ids, dist, stats,
-                         threads, h, target, feat);
+                         threads, h, target, feat, NULL);
     free(ids);
     free(dist);
     return rc;

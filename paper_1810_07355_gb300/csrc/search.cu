@@ -63,9 +63,10 @@ int resident_blocks(const Launch &L, int *per_sm)
 
 // per-warp workspace: visited bitmap (rounded to 256 bytes), id log, candidate spill pool
 int64_t bits_words(int64_t n) { return (n + 8191) / 8192 * 256; }
-size_t slot_bytes(int64_t n)
+int pool_cap(const onng_search_params *p) { return p && p->pool_cap > 0 ? p->pool_cap : kGlobalPool; }
+size_t slot_bytes(int64_t n, int cap)
 {
-    return (size_t)bits_words(n) * sizeof(unsigned) + (size_t)kVisitLog * sizeof(int) + (size_t)kGlobalPool * sizeof(u64);
+    return (size_t)bits_words(n) * sizeof(unsigned) + (size_t)kVisitLog * sizeof(int) + (size_t)cap * sizeof(u64);
 }
 
 }  // namespace
@@ -87,7 +88,7 @@ extern "C" size_t onng_search_workspace_bytes(int64_t nq, const onng_index *idx,
         per_sm = 16;
     const int64_t blocks = std::min<int64_t>(std::max<int64_t>(1, (nq + kWarpsPerCta - 1) / kWarpsPerCta),
                                              (int64_t)per_sm * num_sms());
-    return 1024 + (size_t)blocks * kWarpsPerCta * slot_bytes(idx ? idx->n : 1);
+    return 1024 + (size_t)blocks * kWarpsPerCta * slot_bytes(idx ? idx->n : 1, pool_cap(p));
 }
 
 extern "C" int onng_pad_adjacency(const int64_t *row_ptr, const int32_t *col, int64_t n, int32_t width, int32_t *adj,
@@ -116,6 +117,7 @@ static int search_impl(const onng_index *idx, const float *Q, int64_t nq, const 
     ONNG_REQUIRE(n_seed >= 1 && n_seed <= kMaxSeed, ONNG_E_UNSUPPORTED, "onng_search: n_seed must be in [1, %d]",
                  kMaxSeed);
     ONNG_REQUIRE(!std::isnan(p->eps) && p->eps >= 0, ONNG_E_INVAL, "onng_search: eps must be >= 0");
+    ONNG_REQUIRE(p->pool_cap >= 0 && p->pool_cap <= (1 << 24), ONNG_E_INVAL, "onng_search: pool_cap must be in [0, 2^24]");
     ONNG_REQUIRE(idx->adj == nullptr || idx->adj_width >= 1, ONNG_E_INVAL, "onng_search: adj_width must be >= 1");
     const bool bf16 = p->precision == ONNG_PREC_BF16;
     const bool fp8 = p->precision == ONNG_PREC_FP8;
@@ -147,7 +149,8 @@ static int search_impl(const onng_index *idx, const float *Q, int64_t nq, const 
         return st;
     int64_t blocks = std::min<int64_t>((nq + kWarpsPerCta - 1) / kWarpsPerCta, (int64_t)per_sm * num_sms());
     // the workspace bounds the number of warps (each needs its own spill tables)
-    const size_t per_cta = slot_bytes(idx->n) * kWarpsPerCta;
+    const int cap = pool_cap(p);
+    const size_t per_cta = slot_bytes(idx->n, cap) * kWarpsPerCta;
     const int64_t fit = ws_bytes > 1024 ? (int64_t)((ws_bytes - 1024) / per_cta) : 0;
     blocks = std::min(blocks, fit);
     ONNG_REQUIRE(blocks >= 1, ONNG_E_WORKSPACE, "onng_search: workspace of %zu bytes holds no CTA (%zu needed per CTA)",
@@ -160,7 +163,8 @@ static int search_impl(const onng_index *idx, const float *Q, int64_t nq, const 
     a.bits_words = bits_words(idx->n);
     a.gbits = c.take<unsigned>((size_t)slots * a.bits_words);
     a.glog = c.take<int>((size_t)slots * kVisitLog);
-    a.gpool = c.take<u64>((size_t)slots * kGlobalPool);
+    a.gpool = c.take<u64>((size_t)slots * cap);
+    a.gpool_cap = cap;
     a.row_ptr = idx->row_ptr;
     a.col = idx->col;
     a.adj = idx->adj;
@@ -264,7 +268,9 @@ extern "C" int onng_search_noalloc(const onng_index *idx, const float *Q, int64_
     ONNG_REQUIRE(idx->n > 0 && idx->n <= INT32_MAX, ONNG_E_INVAL, "onng_search_noalloc: bad index size");
     // one CTA's share: the query counter's slot plus kWarpsPerCta per-warp slots
     const size_t cap = (size_t)ONNG_SEARCH_NOALLOC_SCRATCH_BYTES;
-    const size_t need = 1024 + (size_t)kWarpsPerCta * slot_bytes(idx->n);
+    ONNG_REQUIRE(p->pool_cap >= 0 && p->pool_cap <= (1 << 24), ONNG_E_INVAL,
+                 "onng_search_noalloc: pool_cap must be in [0, 2^24]");
+    const size_t need = 1024 + (size_t)kWarpsPerCta * slot_bytes(idx->n, pool_cap(p));
     ONNG_REQUIRE(need <= cap, ONNG_E_WORKSPACE,
                  "onng_search_noalloc: an index of n = %lld needs %zu scratch bytes for one CTA, more than the "
                  "fixed %zu (use onng_search with a caller workspace)",

@@ -111,7 +111,7 @@ template <> struct Tune<__nv_fp8_e4m3> {
     static constexpr int ovf = ONNG_SEARCH_FP8_OVF, gmax = ONNG_SEARCH_FP8_GMAX, minb = ONNG_SEARCH_FP8_MINB;
 };
 constexpr int kVisitLog = 16384;     // ids logged per warp for clearing its bitmap
-constexpr int kGlobalPool = 16384;   // per-warp candidate spill pool entries
+constexpr int kGlobalPool = 16384;   // default per-warp candidate spill pool entries
 constexpr u64 kMaxKey = ~0ull;
 constexpr int kFeat = 16;
 
@@ -146,7 +146,8 @@ struct SearchArgs {
     unsigned *gbits;  // [slots, bits_words]: visited bitmap past the shared table
     int64_t bits_words;
     int *glog;        // [slots, kVisitLog]: ids set in the bitmap
-    u64 *gpool;       // [slots, kGlobalPool]
+    u64 *gpool;       // [slots, gpool_cap]
+    int gpool_cap;    // spill pool entries per warp
 };
 
 template <int HV, int OVF> struct WarpSmem {
@@ -498,12 +499,12 @@ template <int V, class T, int HV, int KR> struct Warp {
             return;
         if (put) {
             int dst = ng + __popc(m & lanemask_lt(lane));
-            if (dst < kGlobalPool)
+            if (dst < a.gpool_cap)
                 gpool[dst] = key;
         }
-        if (ng + __popc(m) > kGlobalPool)
+        if (ng + __popc(m) > a.gpool_cap)
             flags |= ONNG_FLAG_S_OVERFLOW;
-        ng = min(ng + __popc(m), kGlobalPool);
+        ng = min(ng + __popc(m), a.gpool_cap);
     }
 
     // Makes room for `need` (<= 32) more keys in the overflow: drops its
@@ -963,7 +964,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, min_blocks<T>(V, KR)) searc
                      : std::is_same<T, __nv_bfloat16>::value ? static_cast<const void *>(a.Xb)
                                                               : static_cast<const void *>(a.X8);
     Warp<V, T, HV, KR> w(smem[warp], a, xs, lane, a.gbits + slot * a.bits_words, a.glog + slot * kVisitLog,
-                         a.gpool + slot * kGlobalPool);
+                         a.gpool + slot * a.gpool_cap);
     for (;;) {
         int q = 0;
         if (lane == 0)

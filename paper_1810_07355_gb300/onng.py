@@ -38,7 +38,7 @@ class _Index(C.Structure):
 
 class _Params(C.Structure):
     _fields_ = [("k", C.c_int32), ("e_s", C.c_int32), ("eps", C.c_float), ("precision", C.c_int32),
-                ("k_rerank", C.c_int32), ("max_expansions", C.c_int32)]
+                ("k_rerank", C.c_int32), ("max_expansions", C.c_int32), ("pool_cap", C.c_int32)]
 
 
 def library_path() -> str:
@@ -325,8 +325,10 @@ _default_ws = SearchWorkspace()
 def search(index: Index, Q: torch.Tensor, k: int, e_s: int, eps: float, seeds: torch.Tensor,
            precision: int = PREC_FP32, k_rerank: int = 0, eps_q: torch.Tensor | None = None,
            es_q: torch.Tensor | None = None, max_expansions: int = 0, stats: bool = True,
-           workspace: SearchWorkspace | None = None, out=None):
-    """Algorithm 1 for every query row: (ids int32 [nq,k], dist float32 [nq,k], stats int32 [nq,4] or None)."""
+           workspace: SearchWorkspace | None = None, out=None, pool_cap: int = 0):
+    """Algorithm 1 for every query row: (ids int32 [nq,k], dist float32 [nq,k], stats int32 [nq,4] or None).
+
+    ``pool_cap`` sets the per-warp candidate spill-pool entries (0: the library default)."""
     Q = _dev(Q, torch.float32)
     seeds = _dev(seeds, torch.int32)
     nq = Q.shape[0]
@@ -336,7 +338,7 @@ def search(index: Index, Q: torch.Tensor, k: int, e_s: int, eps: float, seeds: t
         index.with_bf16()
     elif precision == PREC_FP8:
         index.with_fp8()
-    p = _Params(k, e_s, float(eps) if math.isfinite(eps) else math.inf, precision, k_rerank, max_expansions)
+    p = _Params(k, e_s, float(eps) if math.isfinite(eps) else math.inf, precision, k_rerank, max_expansions, pool_cap)
     ic = index._c()
     need = lib.onng_search_workspace_bytes(nq, C.byref(ic), C.byref(p))
     ws = (workspace or _default_ws).get(need, dev)

@@ -64,6 +64,10 @@ def test_version_and_argument_checks(lib):
     assert st == onng.ONNG_E_UNSUPPORTED
     st = lib.onng_adjust_degree_count(None, None, -5, 10, 3, 3, None, None, None, 0, None)
     assert st == onng.ONNG_E_INVAL
+    ix = onng._Index(None, None, None, None, None, 100, 128, 0)
+    p = onng._Params(10, 10, 0.1, 0, 0, 0, -1)
+    st = lib.onng_search(C.byref(ix), None, 5, C.byref(p), None, 4, None, None, None, None, None, None, 0, None)
+    assert st == onng.ONNG_E_INVAL and b"pool_cap" in lib.onng_last_error()
 
 
 def test_reduced_precision_argument_checks(lib):

@@ -32,6 +32,64 @@ def test_chain_trace(oracle_lib):
         assert st[0, 1] == c["expansions"]
 
 
+def _chain(g):
+    X = np.array(g["X"], np.float32)
+    n = len(X)
+    rows = [[c for c in (i - 1, i + 1) if 0 <= c < n] for i in range(n)]
+    ptr = np.cumsum([0] + [len(r) for r in rows]).astype(np.int64)
+    col = np.array(sum(rows, []), np.int32)
+    return X, ptr, col
+
+
+def test_chain_margin(oracle_lib):
+    """The smallest relative gap among the comparisons Algorithm 1 decided,
+    traced by hand on the chain (golden values), including an exact tie (0)."""
+    g = json.load(open(os.path.join(GOLDEN, "chain_search.json")))
+    X, ptr, col = _chain(g)
+    Q = np.array([g["query"]], np.float32)
+    for c in g["cases"]:
+        _, _, _, mg = oracle_lib.search(ptr, col, X, Q, g["k"], c["e_s"], g["eps"], np.array([g["seeds"]], np.int32),
+                                        margin=True)
+        np.testing.assert_allclose(mg, [c["margin"]], rtol=1e-6)
+    m = json.load(open(os.path.join(GOLDEN, "chain_margin.json")))
+    ids, dist, st, mg = oracle_lib.search(ptr, col, X, np.array([m["query"]], np.float32), m["k"], m["e_s"], m["eps"],
+                                          np.array([m["seeds"]], np.int32), margin=True)
+    assert ids[0].tolist() == m["ids"]
+    np.testing.assert_allclose(dist[0], m["dist"], rtol=1e-6)
+    assert st[0, 0] == m["distance_computations"] and st[0, 1] == m["expansions"]
+    np.testing.assert_allclose(mg, [m["margin"]], rtol=1e-6)
+    t = m["tie_case"]
+    _, _, _, mg = oracle_lib.search(ptr, col, X, np.array([t["query"]], np.float32), t["k"], t["e_s"], t["eps"],
+                                    np.array([t["seeds"]], np.int32), margin=True)
+    assert mg[0] == t["margin"]
+
+
+def test_margin_leaves_results_unchanged(oracle_lib):
+    """Asking for the margin changes no result or count, and a run whose
+    distances are all integers at least one apart has a margin of at least
+    1 / (largest distance compared)."""
+    X, Q = synth.workload("gmm10k", n=1500, nq=40)
+    ids, dist = oracle_lib.knng(X, 20)
+    ptr, col, _ = oracle_lib.adjust_degree(ids, dist, 8, 16)
+    seeds = oracle_lib.seeds_pivot(X, Q, 64, 5)
+    a = oracle_lib.search(ptr, col, X, Q, 10, 8, 0.1, seeds)
+    b = oracle_lib.search(ptr, col, X, Q, 10, 8, 0.1, seeds, margin=True)
+    for u, v in zip(a, b[:3]):
+        assert np.array_equal(u, v)
+    assert (b[3] >= 0).all() and np.isfinite(b[3]).all()
+    # 1-D points at even integers, queries at odd integers + 0.5: every distance
+    # is an integer + 0.5 and every bound r * 1 too, so two compared values that
+    # differ do so by >= 1
+    P = (2 * np.arange(200, dtype=np.float32))[:, None]
+    rows = [[c for c in (i - 1, i + 1) if 0 <= c < 200] for i in range(200)]
+    ptr1 = np.cumsum([0] + [len(r) for r in rows]).astype(np.int64)
+    col1 = np.array(sum(rows, []), np.int32)
+    Q1 = (2 * np.arange(5, 195, 9, dtype=np.float32) + 0.5)[:, None]
+    s1 = np.full((len(Q1), 1), 0, np.int32)
+    _, d1, _, mg = oracle_lib.search(ptr1, col1, P, Q1, 3, 0, 0.0, s1, margin=True)
+    assert (mg >= 1.0 / 400.0).all()
+
+
 @pytest.fixture(scope="module")
 def one_cluster(oracle_lib):
     X = synth.gaussian_mixture(800, d=16, components=1, sigma=5.0, seed=31)
