@@ -91,6 +91,32 @@ int onng_adjust_degree(const int32_t *nbr, const float *len, int64_t n, int32_t 
                        int32_t e_i, const int64_t *row_ptr, int32_t *col, float *len_out,
                        void *ws, size_t ws_bytes, onng_stream_t stream);
 
+/* --------------------------------------- degree adjustment with constraints
+ * Algorithm 3 (ConstructAdjustedGraphWithConstraint, "SAC"), equal edge for
+ * edge to its sequential greedy pass: G_t = Algorithm 2 with (0, e_i); nodes o in
+ * increasing (|N(G_t, o)|, o) (ties by the smaller id), each taking the members
+ * n of N(G_t, o) in increasing (length, id) and adding o->n when n has no
+ * in-edge yet or (n has fewer than e_i in-edges and o fewer than e_o edges);
+ * then every node with fewer than e_o edges takes its nearest kNN neighbours
+ * not yet in its list.  An edge o->n of the first loop carries the stored
+ * length of n->o.  Rows are ordered by (length, id).
+ * The GPU evaluates the pass per edge: n meets only the nodes of its own first
+ * e_i kNN entries, so the in-degree test never fails, and o->n is added exactly
+ * when n is among o's first e_o members or o is the first node, in the order
+ * above, to meet n.
+ *
+ * onng_adjust_degree_sac_count writes row_ptr [n+1] (and, if nnz_host != NULL,
+ * synchronises and stores the edge count); onng_adjust_degree_sac then fills
+ * col / len_out [nnz].  Input: the kNN lists nbr / len [n, k].
+ */
+size_t onng_adjust_degree_sac_workspace_bytes(int64_t n, int32_t k);
+int onng_adjust_degree_sac_count(const int32_t *nbr, const float *len, int64_t n, int32_t k,
+                                 int32_t e_o, int32_t e_i, int64_t *row_ptr, int64_t *nnz_host,
+                                 void *ws, size_t ws_bytes, onng_stream_t stream);
+int onng_adjust_degree_sac(const int32_t *nbr, const float *len, int64_t n, int32_t k, int32_t e_o,
+                           int32_t e_i, const int64_t *row_ptr, int32_t *col, float *len_out,
+                           void *ws, size_t ws_bytes, onng_stream_t stream);
+
 /* ------------------------------------------------------------ path adjustment
  * Algorithms 4/5 (AdjustPath / HasPath) read order-free: edge (i, j) is dropped
  * when the INPUT graph has i->m and m->j with len(i,m) < len(i,j) and
@@ -104,6 +130,21 @@ size_t onng_adjust_path_workspace_bytes(int64_t n, int64_t nnz);
 int onng_adjust_path(const int64_t *row_ptr, const int32_t *col, const float *len, int64_t n,
                      int64_t *row_ptr_out, int32_t *col_out, float *len_out, int64_t *nnz_host,
                      int32_t *removed_by, void *ws, size_t ws_bytes, onng_stream_t stream);
+
+/* Algorithm 4 (AdjustPath) taken literally, a variant beside the order-free rule
+ * of onng_adjust_path: in round p every node s with more than p edges decides
+ * its p-th input edge (s, t), nodes in ascending id, and keeps it unless
+ * Algorithm 5 finds in the partial output a kept edge (s, m) and a kept edge
+ * (m, t) with len(m, t) < len(s, t).  Kept edges keep their input order; the
+ * result is one round-robin pass of the paper's listing, with node order inside
+ * a round (which the paper leaves open) fixed to ascending ids.  Synchronises
+ * `stream` once per round and pass (rounds = the largest degree).
+ * Outputs as onng_adjust_path (row_ptr_out [n+1]; col_out / len_out sized for
+ * the input edge count; nnz_host optional).  n < 2^31 - 2^23. */
+size_t onng_adjust_path_literal_workspace_bytes(int64_t n, int64_t nnz);
+int onng_adjust_path_literal(const int64_t *row_ptr, const int32_t *col, const float *len, int64_t n,
+                             int64_t *row_ptr_out, int32_t *col_out, float *len_out, int64_t *nnz_host,
+                             void *ws, size_t ws_bytes, onng_stream_t stream);
 
 /* ---------------------------------------------------------------------- seeds
  * onng_seeds_random: the paper's random seeds (Sec. 3): n_seed distinct ids per

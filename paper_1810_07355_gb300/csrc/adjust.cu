@@ -10,6 +10,32 @@
 // register bitonic sort for rows up to 512 edges, an in-place CTA sort for
 // longer rows (hubs).
 //
+// Degree adjustment with constraints (Algorithm 3, "SAC"): its greedy pass reads
+// in a closed form.  N(G_t, o) = { n : o in first_{e_i}(N_k(n)) } (Algorithm 2
+// with (0, e_i)), so a node n is considered only by the nodes of its own first
+// e_i kNN entries, at most e_i of them: the in-degree test |N(G_i, n)| < e_i
+// always holds when n is met.  Taking the nodes o in increasing
+// (|N(G_t, o)|, o) and each list in increasing (length, id), o therefore adds
+// its first e_o members unconditionally and a later member n exactly when no
+// earlier node has added n, i.e. when o is the first of n's considerers in that
+// order (that one always adds n).  Both rules are per-edge, so the pass runs in
+// parallel and equals the sequential one edge for edge.  The last loop then
+// gives every node with fewer than e_o edges its nearest kNN neighbours not yet
+// in its list.
+//
+// Algorithm 4 taken literally (rounds over the partial output; a variant beside
+// the order-free rule below): in round p every node s with more than p input
+// edges decides its p-th edge (s, t) (input rows are in (length, id) order), in
+// ascending s, and keeps it unless HasPath (Algorithm 5) finds, in the partial
+// output G_p, a kept edge (s, m) and a kept edge (m, t) shorter than (s, t).
+// (s, m) was decided in an earlier round; (m, t) sits at m's position r of t:
+// decided when r < p, or earlier in this round when r = p and m < s.  A round
+// first decides every edge whose answer needs no same-round edge, then repeats
+// a resolution pass: an edge waiting on same-round edges of smaller nodes is
+// removed once one of them is kept and kept once all are removed; the smallest
+// waiting node can always be decided, so each pass makes progress.  Positions
+// of t in m's row come from a per-row copy sorted by id (binary search).
+//
 // Path adjustment (Algorithms 4/5, order-free reading): edge (i, j) is dropped
 // if the input graph holds i->m and m->j with len(i,m) < len(i,j) and
 // len(m,j) < len(i,j).  A warp owns a node i: N(i) goes into a shared-memory
@@ -20,6 +46,7 @@
 // compact sequence then writes the kept edges in their input order.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "common.cuh"
 #include "scan.cuh"
@@ -446,6 +473,185 @@ __global__ void path_compact_kernel(const int64_t *__restrict__ rp, const int32_
     }
 }
 
+// ------------------------------------------------------------------ Algorithm 4, literal
+
+// byid[e] = (id << 32 | position) of every edge, per row; sorted per row afterwards
+__global__ void alg4_byid_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, int64_t n,
+                                 unsigned long long *__restrict__ byid)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (i >= n)
+        return;
+    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += 32)
+        byid[e] = ((unsigned long long)(unsigned)col[e] << 32) | (unsigned)(e - rp[i]);
+}
+
+// position of t in row m (its id-sorted copy), or -1
+__device__ __forceinline__ int alg4_find(const int64_t *__restrict__ rp, const unsigned long long *__restrict__ byid,
+                                         int32_t m, int32_t t)
+{
+    int64_t lo = rp[m], hi = rp[m + 1];
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const int32_t id = (int32_t)(byid[mid] >> 32);
+        if (id < t)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    if (lo < rp[m + 1] && (int32_t)(byid[lo] >> 32) == t)
+        return (int)(unsigned)(byid[lo] & 0xFFFFFFFFull);
+    return -1;
+}
+
+// Edge states: 0 undecided, 1 kept, 2 removed.
+// One warp per node s = order[w] (nodes by degree, descending: the nodes with
+// more than p edges are a prefix).  Decides s's p-th edge if it can; counts the
+// edges still waiting in *waiting.
+__global__ void alg4_round_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                  const float *__restrict__ len, const unsigned long long *__restrict__ byid,
+                                  const int32_t *__restrict__ order, int64_t active, int p,
+                                  unsigned char *__restrict__ state, int *__restrict__ waiting)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (w >= active)
+        return;
+    const int32_t s = order[w];
+    const int64_t beg = rp[s];
+    if (state[beg + p] != 0)
+        return;
+    const int32_t t = col[beg + p];
+    const float lst = len[beg + p];
+    bool path = false, wait = false;
+    for (int q0 = 0; q0 < p; q0 += 32) {
+        const int q = q0 + lane;
+        if (q < p && state[beg + q] == 1) {
+            const int32_t m = col[beg + q];
+            const int r = alg4_find(rp, byid, m, t);
+            if (r >= 0 && len[rp[m] + r] < lst) {
+                if (r < p) {
+                    path |= state[rp[m] + r] == 1;
+                } else if (r == p && m < s) {
+                    const unsigned char sm = state[rp[m] + r];
+                    path |= sm == 1;
+                    wait |= sm == 0;
+                }
+            }
+        }
+    }
+    path = __any_sync(0xffffffffu, path);
+    wait = __any_sync(0xffffffffu, wait);
+    if (lane == 0) {
+        if (path)
+            state[beg + p] = 2;
+        else if (!wait)
+            state[beg + p] = 1;
+        else
+            atomicAdd(waiting, 1);
+    }
+}
+
+__global__ void alg4_hist_kernel(const int64_t *__restrict__ rp, int64_t n, int *__restrict__ hist)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&hist[rp[i + 1] - rp[i]], 1);
+}
+
+// order[] = nodes grouped by degree, largest first (offset[d] = nodes of degree > d)
+__global__ void alg4_order_kernel(const int64_t *__restrict__ rp, int64_t n, const int64_t *__restrict__ offset,
+                                  int *__restrict__ cursor, int32_t *__restrict__ order)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = rp[i + 1] - rp[i];
+        order[offset[d] + atomicAdd(&cursor[d], 1)] = (int32_t)i;
+    }
+}
+
+__global__ void alg4_wit_kernel(const unsigned char *__restrict__ state, int64_t nnz, int *__restrict__ wit)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        wit[e] = state[e] == 2 ? 0 : -1;
+}
+
+// ------------------------------------------------------------------ SAC
+
+// first[n] = the first node, in the order (|N(G_t, o)|, o), among the valid ids
+// of first_{fi}(N_k(n)) (-1 if none): the node of Algorithm 3 that meets n first.
+__global__ void sac_first_kernel(const int32_t *__restrict__ nbr, int64_t n, int k, int fi,
+                                 const int64_t *__restrict__ gt_ptr, int32_t *__restrict__ first)
+{
+    for (int64_t y = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; y < n; y += (int64_t)gridDim.x * blockDim.x) {
+        int64_t best_deg = INT64_MAX;
+        int32_t best = -1;
+        for (int p = 0; p < fi; ++p) {
+            const int32_t o = nbr[y * k + p];
+            if (o < 0 || o >= n)
+                continue;
+            const int64_t dg = gt_ptr[o + 1] - gt_ptr[o];
+            if (dg < best_deg || (dg == best_deg && o < best)) {
+                best_deg = dg;
+                best = o;
+            }
+        }
+        first[y] = best;
+    }
+}
+
+// One warp per node o.  Row = the members of N(G_t, o) (keys sorted by (length,
+// id)) at positions < e_o or first-met at o, then, if fewer than e_o, o's kNN
+// neighbours in order that are not in N(G_t, o), up to e_o in all.  Count mode
+// (keys == NULL) writes the row sizes; fill mode writes the keys at row_ptr[o].
+__global__ void sac_row_kernel(const int32_t *__restrict__ nbr, const float *__restrict__ len, int64_t n, int k,
+                               int e_o, const int64_t *__restrict__ gt_ptr,
+                               const unsigned long long *__restrict__ gt_keys, const int32_t *__restrict__ first,
+                               int64_t *__restrict__ cnt, const int64_t *__restrict__ row_ptr,
+                               unsigned long long *__restrict__ keys)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t o = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (o >= n)
+        return;
+    const int64_t beg = gt_ptr[o];
+    const int64_t m = gt_ptr[o + 1] - beg;
+    const int64_t out = keys ? row_ptr[o] : 0;
+    int64_t w = 0;
+    for (int64_t c0 = 0; c0 < m; c0 += 32) {
+        const int64_t p = c0 + lane;
+        unsigned long long key = 0;
+        bool take = false;
+        if (p < m) {
+            key = gt_keys[beg + p];
+            take = p < e_o || first[(int32_t)(unsigned)(key & 0xFFFFFFFFull)] == (int32_t)o;
+        }
+        const unsigned tm = __ballot_sync(0xffffffffu, take);
+        if (keys && take)
+            keys[out + w + __popc(tm & ((1u << lane) - 1u))] = key;
+        w += __popc(tm);
+    }
+    if (m < e_o) {
+        // every member was taken; the nearest kNN neighbours not among them follow
+        for (int p0 = 0; p0 < k && w < e_o; p0 += 32) {
+            const int p = p0 + lane;
+            const int32_t x = p < k ? nbr[o * k + p] : -1;
+            bool cand = x >= 0 && x < n;
+            for (int64_t t = 0; cand && t < m; ++t)
+                cand = (int32_t)(unsigned)(gt_keys[beg + t] & 0xFFFFFFFFull) != x;
+            const unsigned cm = __ballot_sync(0xffffffffu, cand);
+            const int rank = __popc(cm & ((1u << lane) - 1u));
+            if (keys && cand && w + rank < e_o)
+                keys[out + w + rank] = pack_key(len[o * k + p], x);
+            w = min((int64_t)e_o, w + __popc(cm));
+            // kNN rows are padded with -1 at their end: the list stops there
+            if (__ballot_sync(0xffffffffu, p < k && x < 0))
+                break;
+        }
+    }
+    if (!keys && lane == 0)
+        cnt[o] = w;
+}
+
 int grid1d(int64_t work, int threads)
 {
     return (int)std::max<int64_t>(1, std::min<int64_t>((work + threads - 1) / threads, (int64_t)num_sms() * 16));
@@ -545,6 +751,268 @@ extern "C" int onng_adjust_degree(const int32_t *nbr, const float *len, int64_t 
     // the edge count row_ptr[n] is read on the device: no host round trip
     unpack_keys<<<grid1d(n * (int64_t)(fo + fi), 256), 256, 0, s>>>(keys, row_ptr + n, col, len_out);
     return check_launch("onng_adjust_degree: unpack");
+}
+
+// ------------------------------------------------------------------ SAC ABI
+
+namespace onng {
+namespace {
+
+struct SacWs {
+    int *incnt;
+    int64_t *cnt, *big, *gt_ptr;
+    int *n_big;
+    char *scan_ws;
+    size_t scan_bytes;
+    unsigned long long *gt_keys, *keys;
+    int32_t *first;
+    size_t used;
+};
+
+SacWs sac_carve(void *ws, int64_t n, int k)
+{
+    const int64_t nn = std::max<int64_t>(n, 1);
+    WsCarver c(ws);
+    SacWs w;
+    w.incnt = c.take<int>((size_t)nn);
+    w.cnt = c.take<int64_t>((size_t)nn);
+    w.big = c.take<int64_t>((size_t)nn);
+    w.n_big = c.take<int>(64);
+    w.scan_bytes = scan_workspace_bytes(nn + 1);
+    w.scan_ws = c.take<char>(w.scan_bytes);
+    w.gt_ptr = c.take<int64_t>((size_t)nn + 1);
+    w.gt_keys = c.take<unsigned long long>((size_t)nn * std::max(k, 1));
+    w.first = c.take<int32_t>((size_t)nn);
+    w.keys = c.take<unsigned long long>((size_t)nn * std::max(k, 1) * 2);  // rows hold <= n k + n k edges
+    w.used = c.used;
+    return w;
+}
+
+// G_t of Algorithm 3 (Algorithm 2 with (0, e_i)) as sorted (length, id) keys,
+// then every node's first considerer.
+int sac_prepare(const int32_t *nbr, const float *len, int64_t n, int k, int fi, const SacWs &w, cudaStream_t s)
+{
+    ONNG_CUDA_TRY(cudaMemsetAsync(w.incnt, 0, sizeof(int) * n, s), "adjust_degree_sac: clear");
+    ONNG_CUDA_TRY(cudaMemsetAsync(w.n_big, 0, sizeof(int), s), "adjust_degree_sac: clear");
+    degree_count_kernel<<<grid1d(n, 256), 256, 0, s>>>(nbr, n, k, 0, fi, w.cnt, w.incnt);
+    degree_total_kernel<<<grid1d(n, 256), 256, 0, s>>>(nbr, n, k, 0, w.incnt, w.cnt);
+    int st = check_launch("onng_adjust_degree_sac: G_t count");
+    if (st)
+        return st;
+    st = exclusive_scan(w.cnt, w.gt_ptr, n, w.scan_ws, w.scan_bytes, s);
+    if (st)
+        return st;
+    ONNG_CUDA_TRY(cudaMemsetAsync(w.incnt, 0, sizeof(int) * n, s), "adjust_degree_sac: clear");
+    degree_fill_kernel<<<grid1d(n, 256), 256, 0, s>>>(nbr, len, n, k, 0, fi, w.gt_ptr, w.incnt, w.gt_keys);
+    sort_small_rows<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(w.gt_ptr, n, w.gt_keys, w.big, w.n_big);
+    sort_big_rows<<<num_sms() * 2, 1024, 0, s>>>(w.gt_ptr, w.gt_keys, w.big, w.n_big);
+    sac_first_kernel<<<grid1d(n, 256), 256, 0, s>>>(nbr, n, k, fi, w.gt_ptr, w.first);
+    return check_launch("onng_adjust_degree_sac: G_t");
+}
+
+}  // namespace
+}  // namespace onng
+
+extern "C" size_t onng_adjust_degree_sac_workspace_bytes(int64_t n, int32_t k)
+{
+    return sac_carve(nullptr, n, k).used;
+}
+
+extern "C" int onng_adjust_degree_sac_count(const int32_t *nbr, const float *len, int64_t n, int32_t k, int32_t e_o,
+                                            int32_t e_i, int64_t *row_ptr, int64_t *nnz_host, void *ws,
+                                            size_t ws_bytes, onng_stream_t stream)
+{
+    ONNG_REQUIRE(n >= 0 && n <= INT32_MAX && k >= 1 && e_o >= 0 && e_i >= 0, ONNG_E_INVAL,
+                 "onng_adjust_degree_sac_count: bad sizes");
+    ONNG_REQUIRE(n == 0 || (nbr && len), ONNG_E_INVAL, "onng_adjust_degree_sac_count: NULL input");
+    ONNG_REQUIRE(row_ptr, ONNG_E_INVAL, "onng_adjust_degree_sac_count: NULL row_ptr");
+    const size_t need = onng_adjust_degree_sac_workspace_bytes(n, k);
+    ONNG_REQUIRE(ws && ws_bytes >= need, ONNG_E_WORKSPACE, "onng_adjust_degree_sac_count: workspace %zu < %zu bytes",
+                 ws_bytes, need);
+    cudaStream_t s = to_cuda(stream);
+    const SacWs w = sac_carve(ws, n, k);
+    int st;
+    if (n > 0) {
+        st = sac_prepare(nbr, len, n, k, std::min(e_i, k), w, s);
+        if (st)
+            return st;
+        sac_row_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(nbr, len, n, k, e_o, w.gt_ptr, w.gt_keys,
+                                                                       w.first, w.cnt, nullptr, nullptr);
+        st = check_launch("onng_adjust_degree_sac_count: rows");
+        if (st)
+            return st;
+    }
+    st = exclusive_scan(w.cnt, row_ptr, n, w.scan_ws, w.scan_bytes, s);
+    if (st)
+        return st;
+    if (nnz_host) {
+        ONNG_CUDA_TRY(cudaMemcpyAsync(nnz_host, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s),
+                      "adjust_degree_sac: nnz");
+        ONNG_CUDA_TRY(cudaStreamSynchronize(s), "adjust_degree_sac: sync");
+    }
+    return ONNG_OK;
+}
+
+extern "C" int onng_adjust_degree_sac(const int32_t *nbr, const float *len, int64_t n, int32_t k, int32_t e_o,
+                                      int32_t e_i, const int64_t *row_ptr, int32_t *col, float *len_out, void *ws,
+                                      size_t ws_bytes, onng_stream_t stream)
+{
+    ONNG_REQUIRE(n >= 0 && n <= INT32_MAX && k >= 1 && e_o >= 0 && e_i >= 0, ONNG_E_INVAL,
+                 "onng_adjust_degree_sac: bad sizes");
+    ONNG_REQUIRE(n == 0 || (nbr && len), ONNG_E_INVAL, "onng_adjust_degree_sac: NULL input");
+    const size_t need = onng_adjust_degree_sac_workspace_bytes(n, k);
+    ONNG_REQUIRE(ws && ws_bytes >= need, ONNG_E_WORKSPACE, "onng_adjust_degree_sac: workspace %zu < %zu bytes",
+                 ws_bytes, need);
+    if (n == 0)
+        return ONNG_OK;
+    ONNG_REQUIRE(row_ptr && col && len_out, ONNG_E_INVAL, "onng_adjust_degree_sac: NULL output");
+    cudaStream_t s = to_cuda(stream);
+    const SacWs w = sac_carve(ws, n, k);
+    int st = sac_prepare(nbr, len, n, k, std::min(e_i, k), w, s);
+    if (st)
+        return st;
+    sac_row_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(nbr, len, n, k, e_o, w.gt_ptr, w.gt_keys, w.first,
+                                                                   nullptr, row_ptr, w.keys);
+    ONNG_CUDA_TRY(cudaMemsetAsync(w.n_big, 0, sizeof(int), s), "adjust_degree_sac: clear");
+    sort_small_rows<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(row_ptr, n, w.keys, w.big, w.n_big);
+    sort_big_rows<<<num_sms() * 2, 1024, 0, s>>>(row_ptr, w.keys, w.big, w.n_big);
+    st = check_launch("onng_adjust_degree_sac: fill/sort");
+    if (st)
+        return st;
+    unpack_keys<<<grid1d(n * (int64_t)2 * k, 256), 256, 0, s>>>(w.keys, row_ptr + n, col, len_out);
+    return check_launch("onng_adjust_degree_sac: unpack");
+}
+
+// ------------------------------------------------------------------ literal Algorithm 4 ABI
+
+extern "C" size_t onng_adjust_path_literal_workspace_bytes(int64_t n, int64_t nnz)
+{
+    const int64_t nn = std::max<int64_t>(n, 1), mm = std::max<int64_t>(nnz, 1);
+    WsCarver c(nullptr);
+    c.take<unsigned long long>((size_t)mm);  // id-sorted rows
+    c.take<unsigned char>((size_t)mm);       // edge states
+    c.take<int>((size_t)mm);                 // removal marks
+    c.take<int64_t>((size_t)nn);             // kept counts / long rows
+    c.take<int64_t>((size_t)nn + 1);         // degree offsets
+    c.take<int>((size_t)nn + 1);             // degree histogram / cursors
+    c.take<int32_t>((size_t)nn);             // nodes by degree
+    c.take<int>(64);
+    c.take<char>(scan_workspace_bytes(nn + 1));
+    return c.used;
+}
+
+extern "C" int onng_adjust_path_literal(const int64_t *row_ptr, const int32_t *col, const float *len, int64_t n,
+                                        int64_t *row_ptr_out, int32_t *col_out, float *len_out, int64_t *nnz_host,
+                                        void *ws, size_t ws_bytes, onng_stream_t stream)
+{
+    // ids are sorted as (id << 32 | position) keys below the sorters' padding key
+    ONNG_REQUIRE(n >= 0 && n < 0x7F800000LL, ONNG_E_INVAL, "onng_adjust_path_literal: bad n");
+    ONNG_REQUIRE(row_ptr && row_ptr_out, ONNG_E_INVAL, "onng_adjust_path_literal: NULL row_ptr");
+    cudaStream_t s = to_cuda(stream);
+    int64_t nnz = 0;
+    ONNG_CUDA_TRY(cudaMemcpyAsync(&nnz, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s),
+                  "adjust_path_literal: nnz");
+    ONNG_CUDA_TRY(cudaStreamSynchronize(s), "adjust_path_literal: sync");
+    const size_t need = onng_adjust_path_literal_workspace_bytes(n, nnz);
+    ONNG_REQUIRE(ws && ws_bytes >= need, ONNG_E_WORKSPACE, "onng_adjust_path_literal: workspace %zu < %zu bytes",
+                 ws_bytes, need);
+    ONNG_REQUIRE(nnz == 0 || (col && len && col_out && len_out), ONNG_E_INVAL,
+                 "onng_adjust_path_literal: NULL arrays");
+    const int64_t nn = std::max<int64_t>(n, 1), mm = std::max<int64_t>(nnz, 1);
+    WsCarver c(ws);
+    unsigned long long *byid = c.take<unsigned long long>((size_t)mm);
+    unsigned char *state = c.take<unsigned char>((size_t)mm);
+    int *wit = c.take<int>((size_t)mm);
+    int64_t *kept = c.take<int64_t>((size_t)nn);
+    int64_t *offset = c.take<int64_t>((size_t)nn + 1);
+    int *hist = c.take<int>((size_t)nn + 1);
+    int32_t *order = c.take<int32_t>((size_t)nn);
+    int *flags = c.take<int>(64);
+    char *scan_ws = c.take<char>(scan_workspace_bytes(nn + 1));
+    int st;
+    if (n > 0 && nnz > 0) {
+        // rows by id for the position lookups of Algorithm 5
+        ONNG_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * 64, s), "adjust_path_literal: clear");
+        alg4_byid_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(row_ptr, col, n, byid);
+        sort_small_rows<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(row_ptr, n, byid, kept, flags);
+        sort_big_rows<<<num_sms() * 2, 1024, 0, s>>>(row_ptr, byid, kept, flags);
+        // nodes by degree, largest first
+        ONNG_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(int) * (n + 1), s), "adjust_path_literal: clear");
+        alg4_hist_kernel<<<grid1d(n, 256), 256, 0, s>>>(row_ptr, n, hist);
+        ONNG_CUDA_TRY(cudaMemsetAsync(state, 0, (size_t)nnz, s), "adjust_path_literal: clear");
+        st = check_launch("onng_adjust_path_literal: prepare");
+        if (st)
+            return st;
+        std::vector<int> h((size_t)n + 1);
+        ONNG_CUDA_TRY(cudaMemcpyAsync(h.data(), hist, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, s),
+                      "adjust_path_literal: histogram");
+        ONNG_CUDA_TRY(cudaStreamSynchronize(s), "adjust_path_literal: sync");
+        int64_t maxdeg = 0;
+        for (int64_t d = n; d >= 0; --d)
+            if (h[d]) {
+                maxdeg = d;
+                break;
+            }
+        std::vector<int64_t> off((size_t)n + 1, 0), active((size_t)maxdeg + 1, 0);
+        int64_t acc = 0;
+        for (int64_t d = maxdeg; d >= 0; --d) {
+            off[d] = acc;  // nodes of degree > d come first
+            acc += h[d];
+        }
+        for (int64_t p = 0; p <= maxdeg; ++p)
+            active[p] = off[p];  // nodes with more than p edges
+        ONNG_CUDA_TRY(cudaMemcpyAsync(offset, off.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s),
+                      "adjust_path_literal: offsets");
+        ONNG_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(int) * (n + 1), s), "adjust_path_literal: clear");
+        alg4_order_kernel<<<grid1d(n, 256), 256, 0, s>>>(row_ptr, n, offset, hist, order);
+        st = check_launch("onng_adjust_path_literal: order");
+        if (st)
+            return st;
+        int *waiting = flags + 32;
+        for (int64_t p = 0; p < maxdeg; ++p) {
+            const int64_t act = active[p];
+            // every pass decides at least the smallest waiting node, so act + 1 passes suffice
+            for (int64_t pass = 0;; ++pass) {
+                ONNG_REQUIRE(pass <= act, ONNG_E_LIMIT, "onng_adjust_path_literal: round %lld did not settle",
+                             (long long)p);
+                ONNG_CUDA_TRY(cudaMemsetAsync(waiting, 0, sizeof(int), s), "adjust_path_literal: clear");
+                alg4_round_kernel<<<(unsigned)((act * 32 + 255) / 256), 256, 0, s>>>(row_ptr, col, len, byid, order,
+                                                                                  act, (int)p, state, waiting);
+                st = check_launch("onng_adjust_path_literal: round");
+                if (st)
+                    return st;
+                int left = 0;
+                ONNG_CUDA_TRY(cudaMemcpyAsync(&left, waiting, sizeof(int), cudaMemcpyDeviceToHost, s),
+                              "adjust_path_literal: waiting");
+                ONNG_CUDA_TRY(cudaStreamSynchronize(s), "adjust_path_literal: sync");
+                if (left == 0)
+                    break;
+            }
+        }
+        alg4_wit_kernel<<<grid1d(nnz, 256), 256, 0, s>>>(state, nnz, wit);
+        path_count_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(row_ptr, n, wit, kept);
+        st = check_launch("onng_adjust_path_literal: count");
+        if (st)
+            return st;
+    } else if (n > 0) {
+        ONNG_CUDA_TRY(cudaMemsetAsync(kept, 0, sizeof(int64_t) * n, s), "adjust_path_literal: clear");
+    }
+    st = exclusive_scan(kept, row_ptr_out, n, scan_ws, scan_workspace_bytes(nn + 1), s);
+    if (st)
+        return st;
+    if (n > 0 && nnz > 0) {
+        path_compact_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(row_ptr, col, len, n, wit, row_ptr_out,
+                                                                           col_out, len_out, nullptr);
+        st = check_launch("onng_adjust_path_literal: compact");
+        if (st)
+            return st;
+    }
+    if (nnz_host) {
+        ONNG_CUDA_TRY(cudaMemcpyAsync(nnz_host, row_ptr_out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s),
+                      "adjust_path_literal: nnz");
+        ONNG_CUDA_TRY(cudaStreamSynchronize(s), "adjust_path_literal: sync");
+    }
+    return ONNG_OK;
 }
 
 // ------------------------------------------------------------------ path ABI

@@ -66,7 +66,12 @@ def load(build_if_missing: bool = True):
             "onng_adjust_degree_workspace_bytes": ([i64, i32], sz),
             "onng_adjust_degree_count": ([vp, vp, i64, i32, i32, i32, vp, vp, vp, sz, vp], C.c_int),
             "onng_adjust_degree": ([vp, vp, i64, i32, i32, i32, vp, vp, vp, vp, sz, vp], C.c_int),
+            "onng_adjust_degree_sac_workspace_bytes": ([i64, i32], sz),
+            "onng_adjust_degree_sac_count": ([vp, vp, i64, i32, i32, i32, vp, vp, vp, sz, vp], C.c_int),
+            "onng_adjust_degree_sac": ([vp, vp, i64, i32, i32, i32, vp, vp, vp, vp, sz, vp], C.c_int),
             "onng_adjust_path_workspace_bytes": ([i64, i64], sz),
+            "onng_adjust_path_literal_workspace_bytes": ([i64, i64], sz),
+            "onng_adjust_path_literal": ([vp, vp, vp, i64, vp, vp, vp, vp, vp, sz, vp], C.c_int),
             "onng_adjust_path": ([vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, sz, vp], C.c_int),
             "onng_seeds_random": ([u64, i64, i64, i32, vp, vp], C.c_int),
             "onng_seeds_pivot_workspace_bytes": ([i64, i32, i32], sz),
@@ -105,6 +110,8 @@ def exported_symbols():
         "onng_seeds_pivot_workspace_bytes", "onng_seeds_pivot", "onng_search_workspace_bytes", "onng_search",
         "onng_to_bf16", "onng_pad_adjacency", "onng_search_probe", "onng_mlp_nparam", "onng_mlp_forward",
         "onng_mlp_loss_grad", "onng_mlp_adam", "onng_mlp_train", "onng_mlp_predict", "onng_search_noalloc", "onng_to_fp8",
+        "onng_adjust_degree_sac_workspace_bytes", "onng_adjust_degree_sac_count", "onng_adjust_degree_sac",
+        "onng_adjust_path_literal_workspace_bytes", "onng_adjust_path_literal",
     ]
 
 
@@ -181,6 +188,25 @@ def adjust_degree(nbr: torch.Tensor, length: torch.Tensor, e_o: int, e_i: int):
     return row_ptr, col[:nnz.value], ln[:nnz.value]
 
 
+def adjust_degree_sac(nbr: torch.Tensor, length: torch.Tensor, e_o: int, e_i: int):
+    """Algorithm 3 (degree adjustment with constraints) on the GPU: CSR (row_ptr int64, col int32, len float32)."""
+    nbr = _dev(nbr, torch.int32)
+    length = _dev(length, torch.float32)
+    n, k = nbr.shape
+    lib = load()
+    dev = nbr.device
+    ws = _ws(lib.onng_adjust_degree_sac_workspace_bytes(n, k), dev)
+    row_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    nnz = C.c_int64(0)
+    _check(lib.onng_adjust_degree_sac_count(_ptr(nbr), _ptr(length), n, k, e_o, e_i, _ptr(row_ptr), C.byref(nnz),
+                                            _ptr(ws), ws.numel(), _stream()))
+    col = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=dev)
+    ln = torch.empty(max(nnz.value, 1), dtype=torch.float32, device=dev)
+    _check(lib.onng_adjust_degree_sac(_ptr(nbr), _ptr(length), n, k, e_o, e_i, _ptr(row_ptr), _ptr(col), _ptr(ln),
+                                      _ptr(ws), ws.numel(), _stream()))
+    return row_ptr, col[:nnz.value], ln[:nnz.value]
+
+
 def adjust_path(row_ptr: torch.Tensor, col: torch.Tensor, length: torch.Tensor, witnesses: bool = False):
     """Order-free path adjustment on the GPU: CSR (+ witness node per input edge, -1 if kept)."""
     row_ptr = _dev(row_ptr, torch.int64)
@@ -200,6 +226,26 @@ def adjust_path(row_ptr: torch.Tensor, col: torch.Tensor, length: torch.Tensor, 
                                 C.byref(nnz), _ptr(wit), _ptr(ws), ws.numel(), _stream()))
     out = (rp, oc[:nnz.value], ol[:nnz.value])
     return out + (wit[:m],) if witnesses else out
+
+
+def adjust_path_literal(row_ptr: torch.Tensor, col: torch.Tensor, length: torch.Tensor):
+    """Algorithm 4 taken literally (rounds over the partial output, ascending ids
+    inside a round) on the GPU: CSR (row_ptr int64, col int32, len float32)."""
+    row_ptr = _dev(row_ptr, torch.int64)
+    col = _dev(col, torch.int32)
+    length = _dev(length, torch.float32)
+    n = row_ptr.numel() - 1
+    m = col.numel()
+    lib = load()
+    dev = row_ptr.device
+    ws = _ws(lib.onng_adjust_path_literal_workspace_bytes(n, m), dev)
+    rp = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    oc = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+    ol = torch.empty(max(m, 1), dtype=torch.float32, device=dev)
+    nnz = C.c_int64(0)
+    _check(lib.onng_adjust_path_literal(_ptr(row_ptr), _ptr(col), _ptr(length), n, _ptr(rp), _ptr(oc), _ptr(ol),
+                                        C.byref(nnz), _ptr(ws), ws.numel(), _stream()))
+    return rp, oc[:nnz.value], ol[:nnz.value]
 
 
 # ----------------------------------------------------------------------------- seeds

@@ -197,3 +197,50 @@ def test_sac_special_cases_and_invariants(oracle_lib):
     # lengths are the stored kNN lengths of the edge's pair
     d = {(i, j): ln[i, p] for i in range(n) for p, j in enumerate(nbr[i])}
     assert all(np.isclose(lv, d.get((s, c), d.get((c, s)))) for s, c, lv in zip(src, col, l))
+
+
+def _sac_per_edge(nbr, ln, e_o, e_i):
+    """Algorithm 3 evaluated per edge (the form the GPU computes): o keeps the
+    members of N(G_t, o) at positions < e_o, and a later member n when o is the
+    first, in increasing (|N(G_t, x)|, x), of the nodes x that meet n (the valid
+    ids of n's first e_i kNN entries); nodes left below e_o then take their
+    nearest kNN neighbours not yet in the list."""
+    n, k = nbr.shape
+    fi = min(e_i, k)
+    members = [[] for _ in range(n)]
+    for y in range(n):
+        for p in range(fi):
+            if nbr[y, p] >= 0:
+                members[nbr[y, p]].append((ln[y, p], y))
+    for o in range(n):
+        members[o].sort()
+    first = [min(((len(members[o]), o) for o in nbr[y, :fi] if o >= 0), default=(0, -1))[1] for y in range(n)]
+    ptr, col, lens = [0], [], []
+    for o in range(n):
+        row = [(l, y) for p, (l, y) in enumerate(members[o]) if p < e_o or first[y] == o]
+        if len(members[o]) < e_o:
+            have = {y for _, y in members[o]}
+            for p in range(k):
+                if nbr[o, p] < 0 or len(row) >= e_o:
+                    break
+                if nbr[o, p] not in have:
+                    row.append((ln[o, p], nbr[o, p]))
+        row.sort()
+        col += [y for _, y in row]
+        lens += [l for l, _ in row]
+        ptr.append(len(col))
+    return np.array(ptr), np.array(col, dtype=np.int32), np.array(lens)
+
+
+@pytest.mark.parametrize("e_o,e_i", [(5, 10), (10, 5), (0, 8), (8, 0), (3, 3), (12, 12), (20, 30)])
+def test_sac_sequential_pass_equals_per_edge_rule(oracle_lib, e_o, e_i):
+    """The sequential greedy pass of Algorithm 3 (the oracle) and its per-edge
+    reading agree edge for edge, on tie-heavy integer points and on float data:
+    a node is met only by its own first e_i kNN entries, so the in-degree limit
+    e_i never refuses an edge and each decision depends on one edge alone."""
+    for X, k in ((synth.small_integers(700, 4, high=4, seed=3), 12),
+                 (synth.workload("gmm10k", n=900, nq=1)[0], 12)):
+        nbr, ln = oracle_lib.knng(X, k)
+        o = oracle_lib.adjust_degree_sac(nbr, ln, e_o, e_i)
+        c = _sac_per_edge(nbr, ln, e_o, e_i)
+        assert np.array_equal(o[0], c[0]) and np.array_equal(o[1], c[1]) and np.array_equal(o[2], c[2])
