@@ -21,8 +21,8 @@ using InstT = __nv_fp8_e4m3;
 
 template <> Launch pick<InstT, ONNG_INST_V, ONNG_INST_KR>()
 {
-    constexpr size_t sm = sizeof(WarpSmem<ONNG_SEARCH_HV, Tune<InstT>::ovf>) * kWarpsPerCta;
-    return {search_kernel<ONNG_INST_V, InstT, ONNG_SEARCH_HV, ONNG_INST_KR>, sm};
+    constexpr size_t sm = sizeof(WarpSmem<Tune<InstT>::hv, Tune<InstT>::ovf>) * kWarpsPerCta;
+    return {search_kernel<ONNG_INST_V, InstT, Tune<InstT>::hv, ONNG_INST_KR>, sm};
 }
 
 }  // namespace sk

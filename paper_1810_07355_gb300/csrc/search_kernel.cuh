@@ -53,25 +53,45 @@
 #include "common.cuh"
 #include "warp_sort.cuh"
 
-#ifndef ONNG_SEARCH_HV
-#define ONNG_SEARCH_HV 2048
+// Visited set in shared memory: 1 = buckets of 8 ids with two choices per id,
+// 0 = one open-addressing table with linear probing.
+#ifndef ONNG_SEARCH_VISIT
+#define ONNG_SEARCH_VISIT 1
+#endif
+// 1: once the adjacency row of the node expanded next has arrived, ask L2 for
+// its neighbours' vectors (the next round's gathers then start from L2).
+#ifndef ONNG_SEARCH_PREFETCH
+#define ONNG_SEARCH_PREFETCH 1
+#endif
+// Gather slots of a batch: 1 = the new ids go through shared memory in lane
+// order; 0 = each slot finds its lane by a find-first-set on the mask.
+#ifndef ONNG_SEARCH_COMPACT
+#define ONNG_SEARCH_COMPACT 1
 #endif
 #ifndef ONNG_SEARCH_MAXV
 #define ONNG_SEARCH_MAXV 8  // kernels are built for d <= 128 * ONNG_SEARCH_MAXV (1, 2, 4 or 8)
 #endif
-// Per vector type, for d <= 256 and k <= 32: shared-memory overflow keys per
-// warp (a multiple of 64), the most vectors gathered per round (a power of two)
-// and the resident CTAs per SM the registers are sized for.  Float32 vectors
-// (512 B at d = 128) want 16 gathers in flight per lane; bfloat16 vectors are
-// half the size, so fewer gathers per round and more warps per SM pay more.
+// Per vector type, for d <= 256 and k <= 32: visited-table slots per warp (a
+// multiple of 8), shared-memory overflow keys per warp (a power of two >= 64),
+// the most vectors gathered per round (a power of two) and the resident CTAs per
+// SM the registers are sized for.  The search is latency-bound, so resident
+// warps set its speed: float32 vectors (512 B at d = 128) want 16 gathers in
+// flight per lane and run 5 CTAs (20 warps) per SM; bfloat16 vectors are half
+// the size and run 8 gathers per round at 6 CTAs per SM.
+#ifndef ONNG_SEARCH_F32_HV
+#define ONNG_SEARCH_F32_HV 2048
+#endif
 #ifndef ONNG_SEARCH_F32_OVF
-#define ONNG_SEARCH_F32_OVF 256
+#define ONNG_SEARCH_F32_OVF 128
 #endif
 #ifndef ONNG_SEARCH_F32_GMAX
 #define ONNG_SEARCH_F32_GMAX 16
 #endif
 #ifndef ONNG_SEARCH_F32_MINB
-#define ONNG_SEARCH_F32_MINB 4
+#define ONNG_SEARCH_F32_MINB 5
+#endif
+#ifndef ONNG_SEARCH_BF16_HV
+#define ONNG_SEARCH_BF16_HV 2048
 #endif
 #ifndef ONNG_SEARCH_BF16_OVF
 #define ONNG_SEARCH_BF16_OVF 128
@@ -81,6 +101,9 @@
 #endif
 #ifndef ONNG_SEARCH_BF16_MINB
 #define ONNG_SEARCH_BF16_MINB 6
+#endif
+#ifndef ONNG_SEARCH_FP8_HV
+#define ONNG_SEARCH_FP8_HV 2048
 #endif
 #ifndef ONNG_SEARCH_FP8_OVF
 #define ONNG_SEARCH_FP8_OVF 128
@@ -102,13 +125,16 @@ constexpr int kWarpsPerCta = 4;
 constexpr int kMaxK = 128;
 constexpr int kMaxSeed = 64;
 template <class T> struct Tune {
-    static constexpr int ovf = ONNG_SEARCH_F32_OVF, gmax = ONNG_SEARCH_F32_GMAX, minb = ONNG_SEARCH_F32_MINB;
+    static constexpr int hv = ONNG_SEARCH_F32_HV, ovf = ONNG_SEARCH_F32_OVF, gmax = ONNG_SEARCH_F32_GMAX,
+                         minb = ONNG_SEARCH_F32_MINB;
 };
 template <> struct Tune<__nv_bfloat16> {
-    static constexpr int ovf = ONNG_SEARCH_BF16_OVF, gmax = ONNG_SEARCH_BF16_GMAX, minb = ONNG_SEARCH_BF16_MINB;
+    static constexpr int hv = ONNG_SEARCH_BF16_HV, ovf = ONNG_SEARCH_BF16_OVF, gmax = ONNG_SEARCH_BF16_GMAX,
+                         minb = ONNG_SEARCH_BF16_MINB;
 };
 template <> struct Tune<__nv_fp8_e4m3> {
-    static constexpr int ovf = ONNG_SEARCH_FP8_OVF, gmax = ONNG_SEARCH_FP8_GMAX, minb = ONNG_SEARCH_FP8_MINB;
+    static constexpr int hv = ONNG_SEARCH_FP8_HV, ovf = ONNG_SEARCH_FP8_OVF, gmax = ONNG_SEARCH_FP8_GMAX,
+                         minb = ONNG_SEARCH_FP8_MINB;
 };
 constexpr int kVisitLog = 16384;     // ids logged per warp for clearing its bitmap
 constexpr int kGlobalPool = 16384;   // default per-warp candidate spill pool entries
@@ -153,6 +179,7 @@ struct SearchArgs {
 template <int HV, int OVF> struct WarpSmem {
     int vis[HV];
     u64 ovf[OVF];
+    int slot[32];  // ids of a batch's new nodes in lane order (gather slots)
 };
 
 __host__ __device__ constexpr int log2i(int v) { return v <= 1 ? 0 : 1 + log2i(v >> 1); }
@@ -160,6 +187,7 @@ __host__ __device__ constexpr int log2i(int v) { return v <= 1 ? 0 : 1 + log2i(v
 __device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
 
 __device__ __forceinline__ unsigned hash_id(int id) { return static_cast<unsigned>(id) * 0x9E3779B1u; }
+__device__ __forceinline__ unsigned hash2_id(int id) { return (static_cast<unsigned>(id) ^ 0x5BD1E995u) * 0x7FEB352Du; }
 
 __device__ __forceinline__ float key_d2(u64 k) { return __uint_as_float((unsigned)(k >> 32)); }
 __device__ __forceinline__ int key_id(u64 k) { return (int)(unsigned)(k & 0xFFFFFFFFull); }
@@ -289,7 +317,8 @@ __device__ __forceinline__ float sqdiff4(float4 a, float4 b, float acc)
 // Sums v[g] over the warp for G values at once (G a power of two <= 16): each
 // butterfly stage halves the values a lane holds by swapping halves with its
 // partner, then plain butterflies finish.  Afterwards every lane holds the full
-// sum of one value index; holder_lane<G>(g) names a lane holding value g.
+// sum of one value index: value g sits in the lanes whose bits 4 .. 5 - log2 G
+// spell g, lane g << (5 - log2 G) among them.
 template <int G, int OFF> __device__ __forceinline__ void tr_stage(float (&v)[G], int lane, int held)
 {
     const int half = held >> 1;
@@ -323,22 +352,13 @@ template <int G> __device__ __forceinline__ float transpose_reduce(float (&v)[G]
     return s;
 }
 
-template <int G> __device__ __forceinline__ int holder_lane(int g)
-{
-    constexpr int m = log2i(G);
-    int l = 0;
-#pragma unroll
-    for (int t = 0; t < m; ++t)
-        l |= ((g >> (m - 1 - t)) & 1) << (4 - t);
-    return l;
-}
-
 template <int V, class T, int HV, int KR> struct Warp {
     // vectors per gather round: 16 loads in flight per lane at d <= 128
     static constexpr int G0 = V >= 8 ? 2 : V >= 4 ? 4 : V >= 2 ? 8 : 16;
     static constexpr int G = G0 < Tune<T>::gmax ? G0 : Tune<T>::gmax;
     static constexpr int kOvf = Tune<T>::ovf;  // shared-memory overflow keys
     static_assert(kOvf >= 64 && (kOvf & (kOvf - 1)) == 0, "the overflow holds a power of two >= 64 keys");
+    static_assert(HV % 8 == 0, "the visited table holds whole buckets of 8 ids");
     WarpSmem<HV, kOvf> &sm;
     const SearchArgs &a;
     const void *xs;  // vectors the search reads (float32 or bfloat16)
@@ -374,6 +394,7 @@ template <int V, class T, int HV, int KR> struct Warp {
     // Test-and-set of one id by the calling lane; true if newly visited.
     __device__ bool visit(int id)
     {
+        static_assert(ONNG_SEARCH_VISIT == 1 || (HV & (HV - 1)) == 0, "the probing table holds a power of two");
         unsigned h = hash_id(id) >> (32 - log2i(HV));
         for (int t = 0; t < HV; ++t) {
             int v = sm.vis[h];
@@ -401,6 +422,80 @@ template <int V, class T, int HV, int KR> struct Warp {
             spill = true;
     }
 
+    // Appends the ids of the lanes with `set` (bits this warp set) to the bitmap's log.
+    __device__ void log_bits(bool set, int id)
+    {
+        const unsigned m = __ballot_sync(FULL, set);
+        if (set) {
+            const int pos = nlog + __popc(m & lanemask_lt(lane));
+            if (pos < kVisitLog)
+                glog[pos] = id;
+        }
+        nlog += __popc(m);
+    }
+
+    // Test-and-set of a batch (one id per lane, -1 = none) in the bucketed table:
+    // HV / 8 buckets of 8 ids, filled in slot order, two bucket choices per id.
+    // Every lane first looks its id up in both buckets; new ids then take free
+    // slots of their first bucket (lanes aiming at one bucket in lane order),
+    // the rest of their second; an id that finds both full goes to the bitmap,
+    // and so does every later new id of the query.  True if newly visited.
+    __device__ bool visit_batch(int id)
+    {
+        constexpr unsigned NB = HV / 8;
+        // an id held by several lanes (repeated seeds) counts once, at its lowest lane
+        if (__match_any_sync(FULL, id) & lanemask_lt(lane))
+            id = -1;
+        const bool has = id >= 0;
+        const unsigned b1 = has ? __umulhi(hash_id(id), NB) : 0u;
+        const unsigned b2 = has ? __umulhi(hash2_id(id), NB) : 0u;
+        const int4 *bk = reinterpret_cast<const int4 *>(sm.vis);
+        const int4 p0 = bk[2 * b1], p1 = bk[2 * b1 + 1], q0 = bk[2 * b2], q1 = bk[2 * b2 + 1];
+        const bool found = has && (p0.x == id || p0.y == id || p0.z == id || p0.w == id || p1.x == id ||
+                                   p1.y == id || p1.z == id || p1.w == id || q0.x == id || q0.y == id ||
+                                   q0.z == id || q0.w == id || q1.x == id || q1.y == id || q1.z == id || q1.w == id);
+        const bool want = has && !found;
+        if (spill) {
+            const unsigned bit = 1u << (id & 31);
+            const bool isnew = want && (atomicOr(&gbits[id >> 5], bit) & bit) == 0;
+            log_bits(isnew, id);
+            return isnew;
+        }
+        const unsigned wm = __ballot_sync(FULL, want);
+        if (!wm)
+            return false;
+        const int used1 = (p0.x != -1) + (p0.y != -1) + (p0.z != -1) + (p0.w != -1) + (p1.x != -1) +
+                          (p1.y != -1) + (p1.z != -1) + (p1.w != -1);
+        const unsigned g1 = __match_any_sync(FULL, want ? b1 : 0xFFFFFFFFu);
+        const int r1 = __popc(g1 & wm & lanemask_lt(lane));
+        const bool ok1 = want && used1 + r1 < 8;
+        if (ok1)
+            sm.vis[b1 * 8 + used1 + r1] = id;
+        __syncwarp();
+        const bool want2 = want && !ok1;
+        const unsigned wm2 = __ballot_sync(FULL, want2);
+        if (wm2) {
+            const int4 s0 = bk[2 * b2], s1 = bk[2 * b2 + 1];  // after the first-choice stores
+            const int used2 = (s0.x != -1) + (s0.y != -1) + (s0.z != -1) + (s0.w != -1) + (s1.x != -1) +
+                              (s1.y != -1) + (s1.z != -1) + (s1.w != -1);
+            const unsigned g2 = __match_any_sync(FULL, want2 ? b2 : 0xFFFFFFFFu);
+            const int r2 = __popc(g2 & wm2 & lanemask_lt(lane));
+            const bool ok2 = want2 && used2 + r2 < 8;
+            if (ok2)
+                sm.vis[b2 * 8 + used2 + r2] = id;
+            __syncwarp();
+            const bool want3 = want2 && !ok2;
+            if (__ballot_sync(FULL, want3)) {
+                // both buckets full: this id and every later new one go to the bitmap
+                spill = true;
+                if (want3)
+                    atomicOr(&gbits[id >> 5], 1u << (id & 31));
+                log_bits(want3, id);
+            }
+        }
+        return want;
+    }
+
     // Leaves the bitmap all zero for the next query: clears the logged words,
     // or the whole bitmap if the log overflowed.
     __device__ void clear_bits()
@@ -420,25 +515,43 @@ template <int V, class T, int HV, int KR> struct Warp {
     // ---------------------------------------------------------------- distances
 
     // Squared distances of the ids held by the lanes in `mask`; returns this lane's.
+    // The ids go to shared slots in lane order; gather round b takes slots
+    // b .. b + G - 1, every slot loads (empty slots read row 0 and are masked),
+    // so all loads of a round issue back to back.
     template <class L> __device__ float distances(const void *base, int id, unsigned mask)
     {
-        float mine = 0.0f;
         const int chunks = a.d >> 2;
-        while (mask) {
-            // slot g takes the g-th id of the mask; every slot loads (empty slots
-            // read row 0 and are masked), so all loads issue back to back
-            int src[G];
+        const int m = __popc(mask);
+        const bool mine_in = (mask >> lane) & 1u;
+        const int rank = __popc(mask & lanemask_lt(lane));
+#if ONNG_SEARCH_COMPACT
+        if (mine_in)
+            sm.slot[rank] = id;
+        __syncwarp();
+#endif
+        float mine = 0.0f;
+        for (int b0 = 0; b0 < m; b0 += G) {
             int gid[G];
+#if ONNG_SEARCH_COMPACT
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-                src[g] = mask ? __ffs(mask) - 1 : -1;
-                mask &= mask - 1;
+                const int sid = b0 + g < m ? sm.slot[b0 + g] : 0;
+                gid[g] = sid < 0 ? 0 : sid;
             }
+#else
+            {
+                unsigned rest = mask;  // lanes of slots b0 .. : drop the first b0 set bits
+                for (int t = 0; t < b0; ++t)
+                    rest &= rest - 1;
 #pragma unroll
-            for (int g = 0; g < G; ++g) {
-                const int sid = __shfl_sync(FULL, id, src[g] < 0 ? 0 : src[g]);
-                gid[g] = (src[g] < 0 || sid < 0) ? 0 : sid;
+                for (int g = 0; g < G; ++g) {
+                    const int src = rest ? __ffs(rest) - 1 : 0;
+                    rest &= rest - 1;
+                    const int sid = __shfl_sync(FULL, id, src);
+                    gid[g] = (b0 + g < m && sid >= 0) ? sid : 0;
+                }
             }
+#endif
             float4 xv[G][V];
 #pragma unroll
             for (int g = 0; g < G; ++g)
@@ -459,18 +572,18 @@ template <int V, class T, int HV, int KR> struct Warp {
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     int c = lane + 32 * v;
-                    if (src[g] >= 0 && c < chunks)
+                    if (b0 + g < m && c < chunks)
                         acc[g] = sqdiff4(qv[v], xv[g][v], acc[g]);
                 }
             }
-            float red = transpose_reduce<G>(acc, lane);
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                float s = __shfl_sync(FULL, red, holder_lane<G>(g));
-                if (lane == src[g])
-                    mine = s;
-            }
+            const float red = transpose_reduce<G>(acc, lane);
+            // value g of the round sits in lane g << (5 - log2 G)
+            const int r = rank - b0;
+            const float s = __shfl_sync(FULL, red, (r & (G - 1)) << (5 - log2i(G)));
+            if (mine_in && r >= 0 && r < G)
+                mine = s;
         }
+        __syncwarp();
         return mine;
     }
 
@@ -714,6 +827,14 @@ template <int V, class T, int HV, int KR> struct Warp {
     // With `predict`, loads the adjacency row of the node expanded next.
     __device__ void batch(int id, bool init, bool predict)
     {
+#if ONNG_SEARCH_VISIT == 1
+        const bool isnew = visit_batch(id);
+        const unsigned mask = __ballot_sync(FULL, isnew);
+        if (!mask)
+            return;
+        const int nnew = __popc(mask);
+        ndc += nnew;
+#else
         begin_batch();
         bool isnew = id >= 0 && visit(id);
         unsigned mask = __ballot_sync(FULL, isnew);
@@ -729,6 +850,7 @@ template <int V, class T, int HV, int KR> struct Warp {
         } else {
             nvis += nnew;
         }
+#endif
         __syncwarp();
         float d2 = distances<Loader<T>>(xs, id, mask);
         u64 key = pack_key(d2, id);
@@ -741,8 +863,12 @@ template <int V, class T, int HV, int KR> struct Warp {
             seed_cnt += nnew;
         }
         if (predict) {
-            // next pop = min(S head, nearest batch member if it is pushed)
-            const u64 bmin = warp_min_u64(isnew ? key : kMaxKey);
+            // next pop = min(S head, nearest batch member if it is pushed); the
+            // batch minimum by (distance bits, id) from two warp reductions
+            const unsigned dmin = __reduce_min_sync(FULL, isnew ? __float_as_uint(d2) : 0xFFFFFFFFu);
+            const unsigned imin = __reduce_min_sync(FULL, isnew && __float_as_uint(d2) == dmin ? (unsigned)id
+                                                                                               : 0xFFFFFFFFu);
+            const u64 bmin = dmin == 0xFFFFFFFFu ? kMaxKey : ((u64)dmin << 32) | imin;
             const u64 top = __shfl_sync(FULL, head.v[0], 0);
             const u64 next = ((double)key_d2(bmin) <= bound2 && bmin < top) ? bmin : top;
             if (next != kMaxKey) {
@@ -768,6 +894,15 @@ template <int V, class T, int HV, int KR> struct Warp {
         update_bound();
         // S <- S + batch members within r(1+eps)
         pool_push(isnew && (double)d2 <= bound2, key);
+#if ONNG_SEARCH_PREFETCH
+        if (predict && pf_node >= 0 && pf_id >= 0) {
+            // the row of the next node is in: its neighbours' vectors into L2
+            const int bytes = a.d * (int)sizeof(T);  // float32 4, bfloat16 2, e4m3 1 byte per coordinate
+            const char *row = static_cast<const char *>(xs) + (int64_t)pf_id * bytes;
+            for (int off = 0; off < bytes; off += 128)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(row + off));
+        }
+#endif
     }
 
     __device__ void run(int64_t q)
@@ -789,8 +924,8 @@ template <int V, class T, int HV, int KR> struct Warp {
         padded = a.adj != nullptr && es <= a.adj_w;
         const bool predict = padded && es <= 32;
         f2 = isinf(eps) ? INFINITY : (1.0 + (double)eps) * (1.0 + (double)eps);
-        for (int i = lane; i < HV; i += 32)
-            sm.vis[i] = -1;
+        for (int i = lane; i < HV / 4; i += 32)
+            reinterpret_cast<int4 *>(sm.vis)[i] = make_int4(-1, -1, -1, -1);
         head.clear();
         res.clear();
         nh = no = ng = cnt = ndc = nexp = nvis = nlog = nscan = 0;
@@ -944,9 +1079,8 @@ template <int V, class T, int HV, int KR> struct Warp {
     }
 };
 
-// Resident CTAs per SM the register budget is sized for (a few spilled bytes at
-// most).  Shared memory holds 5 CTAs of float32 warps (2048-slot table and 256
-// overflow keys each) or 6 of bfloat16 warps (128 overflow keys).
+// Resident CTAs per SM the register budget is sized for.  Shared memory holds
+// 6 CTAs of warps with a 2048-slot table and 128 overflow keys (37 KB a CTA).
 template <class T> __host__ __device__ constexpr int min_blocks(int V, int KR)
 {
     return V <= 2 && KR == 1 ? Tune<T>::minb : 3;

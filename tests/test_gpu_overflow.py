@@ -80,14 +80,14 @@ def sift6k(onng):
 
 
 def test_pool_overflow_is_flagged_and_stays_in_bounds(onng, sift6k):
-    """pool_cap = 64: the register head (32) and the shared overflow (256 float32
-    keys) hold 288 candidates before the pool is touched, so every query whose
-    oracle candidate set never exceeds 280 must be unflagged and exact; at
+    """pool_cap = 64: the register head (32 keys) and the shared overflow (128
+    keys) hold 160 candidates before the pool is touched, so every query whose
+    oracle candidate set never exceeds 150 must be unflagged and exact; at
     eps = 0.3 every candidate set outgrows the pool."""
     X, Q, g, seeds = sift6k
     idx = onng.Index(g[0], g[1], dev(X))
     nq, k, cap = len(Q), 10, 64
-    for eps, must_flag in ((0.1, False), (0.3, True)):
+    for eps, must_flag in ((0.08, False), (0.3, True)):
         ws = FixedWorkspace(ws_bytes(onng, idx, nq, k, cap))
         out, intact = canaried_out(nq, k)
         ids, dist, st = onng.search(idx, dev(Q), k, 0, eps, seeds, workspace=ws, out=out, pool_cap=cap)
@@ -96,7 +96,7 @@ def test_pool_overflow_is_flagged_and_stays_in_bounds(onng, sift6k):
         o_ids, o_dist, o_st = oracle.search(host(g[0]), host(g[1]), X, Q, k, 0, np.float32(eps), host(seeds))
         ids, dist, st = host(ids), host(dist), host(st)
         flagged = (st[:, 3] & onng.FLAG_S_OVERFLOW) != 0
-        small = o_st[:, 2] <= 280
+        small = o_st[:, 2] <= 150
         assert not flagged[small].any()
         assert np.array_equal(ids[small], o_ids[small])
         assert np.array_equal(st[small, 0], o_st[small, 0])
@@ -105,7 +105,7 @@ def test_pool_overflow_is_flagged_and_stays_in_bounds(onng, sift6k):
         if must_flag:
             assert flagged.sum() >= nq // 2
         else:
-            assert small.mean() > 0.8
+            assert small.mean() > 0.7
 
 
 def test_visited_log_overflow_clears_the_bitmap(onng):

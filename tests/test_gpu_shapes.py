@@ -16,7 +16,7 @@ import pytest
 
 import oracle
 from paper_1810_07355_gb300 import synth
-from parity_helpers import (REL, assert_reranked, assert_rows_near, assert_search_parity, assert_valid_lists,
+from parity_helpers import (DECIDE, REL, assert_reranked, assert_rows_near, assert_search_parity, assert_valid_lists,
                             d64)
 
 torch = pytest.importorskip("torch")
@@ -151,7 +151,7 @@ def test_search_integer_fp8_at_d(onng, int_graph):
                                         margin=True)
     ids, dist, st = host(ids), host(dist), host(st)
     assert_valid_lists(ids, dist, X, Q)
-    tf = mg > REL
+    tf = mg > DECIDE
     assert tf.mean() >= 0.5
     assert np.array_equal(st[tf, 0], o_st[tf, 0]) and np.array_equal(st[tf, 1], o_st[tf, 1])
     assert_reranked(ids[tf], dist[tf], cand[tf], X, Q[tf], 10)
@@ -196,7 +196,7 @@ def test_search_reduced_float_at_d(onng, float_graph, prec):
                                           margin=True)
         ids, dist, st = host(ids), host(dist), host(st)
         assert_valid_lists(ids, dist, X, Q)
-        tf = mg > REL
+        tf = mg > DECIDE
         assert tf.mean() >= 0.3, tf.mean()
         assert np.array_equal(st[tf, 0], o_st[tf, 0]) and np.array_equal(st[tf, 1], o_st[tf, 1])
         assert_reranked(ids[tf], dist[tf], cand[tf], X, Q[tf], 10)
