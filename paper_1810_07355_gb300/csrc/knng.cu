@@ -265,10 +265,10 @@ __global__ void knn_final_kernel(const float *__restrict__ X, int d, const float
 // ---------------------------------------------------------------- tensor cores
 //
 // knn_tc_kernel: the same sweep with the dot products on the 5th-generation
-// tensor cores, for inputs that are exact in bfloat16 (integers in [-256, 256]
-// with squared norms below 2^24, e.g. 8-bit image descriptors): then every
-// product and partial sum is an integer below 2^24 and the float32
-// accumulation, hence the ranking, is exact.
+// tensor cores, for byte-valued inputs (integers in [0, 255], e.g. 8-bit image
+// descriptors) at d = 64 or 128: they are exact in bfloat16, every product and
+// partial sum is an integer below 2^23, so the float32 accumulation, and with it
+// the ranking, is exact.
 //
 // One CTA owns 128 query rows (the A operand, loaded once by TMA) and sweeps the
 // base in tiles of 256 rows (the B operand, a two-stage TMA ring).  Shared
@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const float qnr = row_ok ? qn[grow] : 0.f;
         const int64_t self = (self_offset >= 0 && row_ok) ? self_offset + grow : -1;
         float thr = row_ok ? INFINITY : -INFINITY;
-        s_xn[tid] = tid < n ? xn[tid] : INFINITY;
+        s_xn[tid] = tid < n ? 0.5f * xn[tid] : INFINITY;
         epi_sync();
         for (int64_t t = 0; t < tiles; ++t) {
             const int b = (int)(t & 1);
@@ -546,39 +546,47 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 break;
             tc_fence_after();
             const int64_t col0 = t * TC_N + half * 128;
-            const float *xs = s_xn + b * TC_N + half * 128;
+            const float *hs = s_xn + b * TC_N + half * 128;  // |x|^2 / 2 of the tile's columns
             const int64_t self_local = self - col0;  // in [0, 128) when the self column is here
+            // d^2 = |q|^2 + |x|^2 - 2 q.x < thr  <=>  q.x - |x|^2 / 2 > (|q|^2 - thr) / 2, every term
+            // an exact integer or half-integer here; the running maximum of the left side
+            // decides a chunk, and only a chunk with a hit forms distances
+            const float tr = 0.5f * (qnr - thr);
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 uint32_t v[32];
                 tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * TC_N + half * 128 + c * 32), v);
-                float d2[32];
+                float mx = -INFINITY;
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    mx = fmaxf(mx, __uint_as_float(v[j]) - hs[c * 32 + j]);
+                if (!(mx > tr))
+                    continue;
                 uint32_t hit = 0;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    d2[j] = fmaxf(qnr + xs[c * 32 + j] - 2.f * __uint_as_float(v[j]), 0.f);
-                    hit |= (d2[j] < thr ? 1u : 0u) << j;
-                }
+                for (int j = 0; j < 32; ++j)
+                    hit |= (__uint_as_float(v[j]) - hs[c * 32 + j] > tr ? 1u : 0u) << j;
                 const int64_t sj = self_local - c * 32;
                 if (sj >= 0 && sj < 32)
                     hit &= ~(1u << (int)sj);
                 while (hit) {
                     const int j = __ffs(hit) - 1;
                     hit &= hit - 1;
-                    float dj = d2[0];
+                    float aj = __uint_as_float(v[0]) - hs[c * 32];
 #pragma unroll
                     for (int u = 1; u < 32; ++u)
-                        dj = u == j ? d2[u] : dj;
+                        aj = u == j ? __uint_as_float(v[u]) - hs[c * 32 + u] : aj;
+                    const float dj = fmaxf(qnr - 2.f * aj, 0.f);
                     const int pos = atomicAdd(&s_cnt[r], 1);
                     buf[grow * TC_BUF + pos] = pack_key(dj, (int)(col0 + c * 32 + j));
                 }
             }
             tc_fence_before();
             mbar_arrive(&acce[b]);
-            // stage the next tile's norms into the other half of s_xn
+            // stage the next tile's half norms into the other half of s_xn
             {
                 const int64_t nc = (t + 1) * TC_N + tid;
-                s_xn[(b ^ 1) * TC_N + tid] = nc < n ? xn[nc] : INFINITY;
+                s_xn[(b ^ 1) * TC_N + tid] = nc < n ? 0.5f * xn[nc] : INFINITY;
             }
             epi_sync();
             const bool last = t + 1 == tiles;
@@ -603,13 +611,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
-// Sets *flag if any of the values is not an integer in [-256, 256].
+// Sets *flag if any of the values is not an integer in [0, 255] (byte-valued
+// descriptors: exact in bfloat16, and at d <= 128 every squared norm, dot product,
+// |x|^2 / 2 and distance of the tensor-core path is an exact float32 below 2^23).
 __global__ void bf16_exact_kernel(const float *__restrict__ x, int64_t count, int *flag)
 {
     int bad = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
         const float v = x[i];
-        bad |= !(v == rintf(v) && fabsf(v) <= 256.f);
+        bad |= !(v == rintf(v) && v >= 0.f && v <= 255.f);
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0)
         atomicOr(flag, 1);
@@ -780,7 +790,7 @@ extern "C" int onng_knn(const float *X, int64_t n, int32_t d, const float *Q, in
     int st = check_launch("onng_knn: norms");
     if (st)
         return st;
-    // tensor-core path: d of 64 or 128, k + 16 <= 128, values exact in bfloat16
+    // tensor-core path: d of 64 or 128, k + 16 <= 128, byte-valued inputs
     if (n > 0 && (d == 64 || d == 128) && kc <= 128 && n <= INT32_MAX - TC_N) {
         ONNG_CUDA_TRY(cudaMemsetAsync(flags, 0, 64 * sizeof(int), s), "onng_knn: clear flags");
         const int gb = num_sms() * 8;
