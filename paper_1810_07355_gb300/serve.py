@@ -3,13 +3,21 @@
 Requests (a few queries each, with their own k and required recall) arrive over
 time.  The loop groups pending requests by (k, recall) class, since one search
 launch runs one k and one eps, and keeps up to `slots` launches in flight, each
-on its own CUDA stream with its own fixed workspace, query, seed and result
-buffers.  A slot is free again once its launch's results are back on the host;
-requests that arrived meanwhile are admitted into the next free slot, so the
-work of several batches overlaps on the device.  Admission is bounded by device
-memory: the workspace budget is split across the slots, and the search sizes
-its grid to the workspace it is given (a smaller workspace means fewer resident
-warps, never a failure).
+on its own CUDA stream with its own query, seed and result buffers.  A slot is
+free again once its launch's results are back on the host; requests that
+arrived meanwhile are admitted into the next free slot, so the work of several
+batches overlaps on the device.
+
+Admission is by device workspace: all launches draw their search workspace from
+one budget (a first-fit pool over a single device buffer).  A batch is admitted
+when the pool can give it the workspace its grid needs (the library's
+onng_search_workspace_bytes for that batch); when nothing else is in flight it
+takes what the pool has, down to one CTA's worth (the search then runs fewer
+warps, never fails).  The pool returns a launch's range when its results are on
+the host.
+
+A host watchdog bounds every launch: one whose results have not arrived within
+`timeout_s` stops the loop with ServeTimeout, naming the batch.
 
 Each query's result depends only on the query, its seeds, k, eps, e_s and the
 precision, never on what it is batched with; the tests check that every
@@ -71,10 +79,49 @@ class Scheduler:
         return Batch(cls, reqs, rows, nq)
 
 
+class ServeTimeout(RuntimeError):
+    """A launch did not complete within the watchdog's limit."""
+
+
+class WorkspacePool:
+    """First-fit allocator over `budget` bytes of one device buffer (offsets
+    aligned to 256 bytes).  alloc returns an offset or None; free returns a range."""
+
+    def __init__(self, budget: int, device):
+        self.budget = int(budget) // 256 * 256
+        self.buf = torch.empty(max(self.budget, 256), dtype=torch.uint8, device=device)
+        self.free_list = [(0, self.budget)]  # sorted (offset, size)
+
+    def alloc(self, nbytes: int):
+        need = (int(nbytes) + 255) // 256 * 256
+        for i, (off, size) in enumerate(self.free_list):
+            if size >= need:
+                rest = (off + need, size - need)
+                self.free_list[i:i + 1] = [rest] if rest[1] else []
+                return off
+        return None
+
+    def largest(self) -> int:
+        return max((size for _, size in self.free_list), default=0)
+
+    def free(self, off: int, nbytes: int):
+        need = (int(nbytes) + 255) // 256 * 256
+        fl = sorted(self.free_list + [(off, need)])
+        merged = []
+        for o, sz in fl:
+            if merged and merged[-1][0] + merged[-1][1] == o:
+                merged[-1] = (merged[-1][0], merged[-1][1] + sz)
+            else:
+                merged.append((o, sz))
+        self.free_list = merged
+
+    def in_use(self) -> int:
+        return self.budget - sum(size for _, size in self.free_list)
+
+
 @dataclass
 class _Slot:
     stream: torch.cuda.Stream
-    ws: torch.Tensor
     q_host: torch.Tensor
     q_dev: torch.Tensor
     seeds: torch.Tensor
@@ -84,6 +131,9 @@ class _Slot:
     dist_host: torch.Tensor
     event: torch.cuda.Event = None
     batch: Batch = None
+    ws_off: int = -1
+    ws_bytes: int = 0
+    deadline: float = 0.0
 
 
 @dataclass
@@ -93,13 +143,16 @@ class ServeResult:
     latency: dict = field(default_factory=dict)  # request -> seconds from arrival to results on the host
     launches: int = 0
     wall: float = 0.0
+    ws_peak: int = 0        # most workspace bytes in use at once
+    ws_waits: int = 0       # times a batch waited for workspace
 
     def summary(self, trace) -> dict:
         lat = np.array([self.latency[i] for i in range(len(trace))]) * 1e3
         queries = int(trace["size"].sum())
         return {"requests": len(trace), "queries": queries, "launches": self.launches,
                 "queries_per_s": round(queries / self.wall, 1), "p50_ms": round(float(np.percentile(lat, 50)), 3),
-                "p99_ms": round(float(np.percentile(lat, 99)), 3), "wall_s": round(self.wall, 3)}
+                "p99_ms": round(float(np.percentile(lat, 99)), 3), "wall_s": round(self.wall, 3),
+                "workspace_peak_bytes": self.ws_peak, "workspace_waits": self.ws_waits}
 
 
 class Server:
@@ -107,7 +160,7 @@ class Server:
 
     def __init__(self, index: onng.Index, eps_table: dict, e_s: int, n_pivot: int = 256, n_seed: int = 10,
                  precision: int = onng.PREC_FP32, k_rerank: int = 0, slots: int = 4, ws_budget: int = 1 << 30,
-                 max_queries: int = 4096, k_max: int = 100):
+                 max_queries: int = 4096, k_max: int = 100, timeout_s: float = 10.0):
         self.lib = onng.load()
         self.index = (index.with_bf16() if precision == onng.PREC_BF16 else
                       index.with_fp8() if precision == onng.PREC_FP8 else index)
@@ -118,19 +171,17 @@ class Server:
         dev = index.X.device
         d = index.X.shape[1]
         ic = self.index._c()
+        self.timeout_s = timeout_s
         p = onng._Params(k_max, e_s, 0.0, precision, max(k_rerank, k_max), 0)
         # eps_table values: eps (with e_s) or (eps, e_s) per (k, recall) class
-        full = self.lib.onng_search_workspace_bytes(max_queries, C.byref(ic), C.byref(p))
-        one_cta = self.lib.onng_search_workspace_bytes(1, C.byref(ic), C.byref(p))
-        self.ws_bytes = int(min(full, ws_budget // slots))
-        if self.ws_bytes < one_cta:
-            raise ValueError(f"workspace budget {ws_budget} B over {slots} slots is below one search CTA "
-                             f"({one_cta} B per slot)")
+        self.one_cta = int(self.lib.onng_search_workspace_bytes(1, C.byref(ic), C.byref(p)))
+        if ws_budget < self.one_cta:
+            raise ValueError(f"workspace budget {ws_budget} B is below one search CTA ({self.one_cta} B)")
+        self.pool = WorkspacePool(ws_budget, dev)
         self.slots = []
         for _ in range(slots):
             self.slots.append(_Slot(
                 stream=torch.cuda.Stream(device=dev),
-                ws=torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev),
                 q_host=torch.empty((max_queries, d), dtype=torch.float32).pin_memory(),
                 q_dev=torch.empty((max_queries, d), dtype=torch.float32, device=dev),
                 seeds=torch.empty(max_queries * n_seed, dtype=torch.int32, device=dev),
@@ -139,7 +190,29 @@ class Server:
                 ids_host=torch.empty(max_queries * k_max, dtype=torch.int32).pin_memory(),
                 dist_host=torch.empty(max_queries * k_max, dtype=torch.float32).pin_memory()))
 
-    def _launch(self, s: _Slot, b: Batch, Q: np.ndarray):
+    def _need(self, b: Batch) -> int:
+        """Workspace bytes the search grid of batch b needs."""
+        k, recall = b.cls
+        eps, e_s = self._params(k, recall)
+        p = onng._Params(k, e_s, eps, self.precision, max(self.k_rerank, k) if self.precision else 0, 0)
+        ic = self.index._c()
+        return int(self.lib.onng_search_workspace_bytes(b.nq, C.byref(ic), C.byref(p)))
+
+    def _reserve(self, b: Batch, idle: bool):
+        """(offset, bytes) of workspace for batch b, or None to wait: the grid's
+        full need, or, when nothing is in flight, the largest free range (at least
+        one CTA's worth)."""
+        need = self._need(b)
+        off = self.pool.alloc(need)
+        if off is not None:
+            return off, need
+        if idle:
+            got = min(need, self.pool.largest())
+            if got >= self.one_cta:
+                return self.pool.alloc(got), got
+        return None
+
+    def _launch(self, s: _Slot, b: Batch, Q: np.ndarray, ws_off: int, ws_bytes: int):
         k, recall = b.cls
         eps, e_s = self._params(k, recall)
         qh = s.q_host.numpy()
@@ -155,14 +228,15 @@ class Server:
             s.q_dev[:b.nq].copy_(s.q_host[:b.nq], non_blocking=True)
             onng._check(self.lib.onng_seeds_pivot(onng._ptr(X), X.shape[0], X.shape[1], onng._ptr(s.q_dev), b.nq,
                                                   self.n_pivot, self.n_seed, onng._ptr(s.seeds), None, 0, st))
+            ws = C.c_void_p(self.pool.buf.data_ptr() + ws_off)
             onng._check(self.lib.onng_search(C.byref(ic), onng._ptr(s.q_dev), b.nq, C.byref(p), onng._ptr(s.seeds),
                                              self.n_seed, None, None, onng._ptr(s.ids_dev), onng._ptr(s.dist_dev),
-                                             None, onng._ptr(s.ws), self.ws_bytes, st))
+                                             None, ws, ws_bytes, st))
             s.ids_host[:b.nq * k].copy_(s.ids_dev[:b.nq * k], non_blocking=True)
             s.dist_host[:b.nq * k].copy_(s.dist_dev[:b.nq * k], non_blocking=True)
             s.event = torch.cuda.Event()
             s.event.record(s.stream)
-        s.batch = b
+        s.batch, s.ws_off, s.ws_bytes = b, ws_off, ws_bytes
 
     def _params(self, k, recall):
         v = self.eps_table[(int(k), float(recall))]
@@ -179,7 +253,8 @@ class Server:
             out.dist[rid] = dist[o:o + size].copy()
             out.latency[rid] = now - trace["arrival"][rid]
             o += size
-        s.batch, s.event = None, None
+        self.pool.free(s.ws_off, s.ws_bytes)
+        s.batch, s.event, s.ws_off, s.ws_bytes = None, None, -1, 0
 
     def run(self, trace, Q: np.ndarray) -> ServeResult:
         """Serves `trace` (synth.request_trace rows) in real time; Q holds the queries."""
@@ -189,6 +264,7 @@ class Server:
             raise ValueError("a request's k exceeds k_max")
         out, sched = ServeResult(), Scheduler()
         n, nxt, done = len(trace), 0, 0
+        held = None  # a batch taken from the scheduler that waits for workspace
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         while done < n:
@@ -199,15 +275,32 @@ class Server:
                 nxt += 1
             progress = False
             for s in self.slots:
-                if s.batch is not None and s.event.query():
+                if s.batch is None:
+                    continue
+                if s.event.query():
                     done += len(s.batch.reqs)
                     self._collect(s, out, trace, time.perf_counter() - t0)
                     progress = True
+                elif time.perf_counter() > s.deadline:
+                    raise ServeTimeout(f"batch of {s.batch.nq} queries (class {s.batch.cls}, requests "
+                                       f"{s.batch.reqs[:4]}...) not done after {self.timeout_s} s")
             for s in self.slots:
-                if s.batch is None and len(sched):
-                    self._launch(s, sched.next_batch(self.max_queries), Q)
-                    out.launches += 1
-                    progress = True
+                if s.batch is not None or (held is None and not len(sched)):
+                    continue
+                b = held if held is not None else sched.next_batch(self.max_queries)
+                idle = all(x.batch is None for x in self.slots)
+                got = self._reserve(b, idle)
+                if got is None:
+                    if held is None:
+                        out.ws_waits += 1
+                    held = b
+                    break
+                held = None
+                self._launch(s, b, Q, *got)
+                s.deadline = time.perf_counter() + self.timeout_s
+                out.launches += 1
+                out.ws_peak = max(out.ws_peak, self.pool.in_use())
+                progress = True
             if not progress:
                 time.sleep(2e-5)
         out.wall = time.perf_counter() - t0
@@ -218,11 +311,13 @@ class Server:
         alone-versus-in-the-mix test)."""
         s = self.slots[0]
         b = Batch((int(k), float(recall)), [0], [(0, len(Q))], len(Q))
-        self._launch(s, b, Q)
+        got = self._reserve(b, True)
+        self._launch(s, b, Q, *got)
         s.event.synchronize()
         ids = s.ids_host[:b.nq * k].numpy().reshape(b.nq, k).copy()
         dist = s.dist_host[:b.nq * k].numpy().reshape(b.nq, k).copy()
-        s.batch, s.event = None, None
+        self.pool.free(s.ws_off, s.ws_bytes)
+        s.batch, s.event, s.ws_off, s.ws_bytes = None, None, -1, 0
         return ids, dist
 
 
@@ -262,64 +357,76 @@ def calibrate_eps(index, Q, k_values, recalls, e_s_options, n_pivot, n_seed, pre
     return table
 
 
-def main():
+def serve_spec(seconds: float = 60.0, rate: float = 100_000.0, precisions=("fp8", "bf16"), slots: int = 4,
+               ws_mb: int = 1024, e_s: int = 10, k_rerank: int = 32, capacity_rate: float = 0.0,
+               timeout_s: float = 10.0) -> dict:
+    """The serving measurement: the 10k x 128 Gaussian-mixture index (k = 40
+    graph, e_o = 10, e_i = 30, path adjustment) with bfloat16 and FP8 copies, a
+    seeded Poisson trace of `seconds` at `rate` queries/s (requests of 1-256
+    queries, log-uniform; k in {1, 10, 100}; recall in {0.9, 0.95, 0.99}), served
+    in real time by the continuous-batching loop in each reduced precision and by
+    one-slot batched fp32 search; per run queries/s and p50 / p99 request latency,
+    and a sample of requests searched alone for the same-in-the-mix check."""
     from . import synth
-    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("--seconds", type=float, default=10.0)
-    ap.add_argument("--rate", type=float, default=100_000.0, help="mean offered queries/s")
-    ap.add_argument("--slots", type=int, default=4)
-    ap.add_argument("--ws-mb", type=int, default=1024, help="device workspace budget over all slots (MB)")
-    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
-    ap.add_argument("--e-s", type=int, default=10, help="first e_s tried per class (then 2x, 4x, every edge)")
-    ap.add_argument("--k-rerank", type=int, default=32, help="float32 rerank of max(k, this) in bf16 / fp8")
-    ap.add_argument("--capacity-rate", type=float, default=2_000_000.0,
-                    help="offered load of a second, saturating run (0: skip)")
-    a = ap.parse_args()
     dev = torch.device("cuda")
     X, Qcal = synth.workload("gmm10k", nq=2000)
-    trace = synth.request_trace(a.seconds, a.rate)
+    trace = synth.request_trace(seconds, rate)
     queries = int(trace["size"].sum())
     _, Q = synth.workload("gmm10k", nq=queries)
     Xd = torch.from_numpy(X).to(dev)
     nbr, ln = onng.build_knng(Xd, 40)
     g = onng.adjust_path(*onng.adjust_degree(nbr, ln, 10, 30))
-    index = onng.Index(g[0], g[1], Xd).with_adjacency(a.e_s)
-    prec = {"fp32": onng.PREC_FP32, "bf16": onng.PREC_BF16, "fp8": onng.PREC_FP8}[a.precision]
+    index = onng.Index(g[0], g[1], Xd).with_adjacency(e_s)
     ks, recalls = (1, 10, 100), (0.9, 0.95, 0.99)
-    es_opts = (a.e_s, 2 * a.e_s, 4 * a.e_s, 0)
-    kr = a.k_rerank if prec != onng.PREC_FP32 else 0
-    table = calibrate_eps(index, Qcal, ks, recalls, es_opts, 256, 10, prec, kr)
-    table32 = calibrate_eps(index, Qcal, ks, recalls, es_opts, 256, 10)
-    budget = a.ws_mb << 20
-    srv = Server(index, table, a.e_s, precision=prec, k_rerank=kr, slots=a.slots, ws_budget=budget)
-    srv.run(trace[: min(len(trace), 200)], Q)  # warm-up
-    res = srv.run(trace, Q)
-    base = Server(index, table32, a.e_s, slots=1, ws_budget=budget)
-    base.run(trace[: min(len(trace), 200)], Q)
-    res0 = base.run(trace, Q)
-    # a sample of requests searched alone must give the same results as in the mix
+    es_opts = (e_s, 2 * e_s, 4 * e_s, 0)
+    budget = ws_mb << 20
+    codes = {"fp32": onng.PREC_FP32, "bf16": onng.PREC_BF16, "fp8": onng.PREC_FP8}
+    runs, tables, same = {}, {}, {}
     rng = np.random.default_rng(0)
-    same = 0
     sample = rng.choice(len(trace), size=min(200, len(trace)), replace=False)
-    for rid in sample:
-        r = trace[rid]
-        ids, dist = srv.search_alone(Q[r["first"]:r["first"] + r["size"]], int(r["k"]), float(r["recall"]))
-        same += int(np.array_equal(ids, res.ids[rid]) and np.array_equal(dist, res.dist[rid]))
-    capacity = None
-    if a.capacity_rate > 0:
-        ctrace = synth.request_trace(min(a.seconds, 2.0), a.capacity_rate, seed=synth.SEED_BASE + 6)
-        _, CQ = synth.workload("gmm10k", nq=int(ctrace["size"].sum()))
-        capacity = {"offered_qps": a.capacity_rate, "served": srv.run(ctrace, CQ).summary(ctrace),
-                    "batched_fp32_one_slot": base.run(ctrace, CQ).summary(ctrace)}
-    line = {"metric": "serving: queries/s and p50/p99 request latency, continuous batching",
-            "index": "gmm10k n=10000 d=128 (k=40 graph, e_o=10, e_i=30, path adjustment)",
-            "trace": {"seconds": a.seconds, "offered_qps": a.rate, "requests": len(trace), "queries": queries,
-                      "sizes": "log-uniform 1..256", "k": list(ks), "recall": list(recalls)},
-            "served": dict(res.summary(trace), precision=a.precision, k_rerank=kr, slots=a.slots, ws_mb=a.ws_mb,
-                           ws_bytes_per_slot=srv.ws_bytes),
-            "batched_fp32_one_slot": res0.summary(trace), "capacity": capacity,
-            "eps_e_s_table": {f"k={k},recall={t}": [round(v[0], 4), v[1]] for (k, t), v in table.items()},
-            "same_alone_and_in_mix": f"{same}/{len(sample)}"}
+    for name in tuple(precisions) + ("fp32",):
+        prec = codes[name]
+        kr = k_rerank if prec != onng.PREC_FP32 else 0
+        table = calibrate_eps(index, Qcal, ks, recalls, es_opts, 256, 10, prec, kr)
+        srv = Server(index, table, e_s, precision=prec, k_rerank=kr, slots=1 if name == "fp32" else slots,
+                     ws_budget=budget, timeout_s=timeout_s)
+        srv.run(trace[: min(len(trace), 200)], Q)  # warm-up
+        res = srv.run(trace, Q)
+        key = "batched_fp32_one_slot" if name == "fp32" else name
+        runs[key] = dict(res.summary(trace), precision=name, k_rerank=kr, slots=len(srv.slots), ws_budget_mb=ws_mb)
+        tables[name] = {f"k={k},recall={t}": [round(v[0], 4), v[1]] for (k, t), v in table.items()}
+        ok = 0
+        for rid in sample:
+            r = trace[rid]
+            ids, dist = srv.search_alone(Q[r["first"]:r["first"] + r["size"]], int(r["k"]), float(r["recall"]))
+            ok += int(np.array_equal(ids, res.ids[rid]) and np.array_equal(dist, res.dist[rid]))
+        same[key] = f"{ok}/{len(sample)}"
+        if capacity_rate > 0 and name != "fp32":
+            ctrace = synth.request_trace(min(seconds, 2.0), capacity_rate, seed=synth.SEED_BASE + 6)
+            _, CQ = synth.workload("gmm10k", nq=int(ctrace["size"].sum()))
+            runs[key]["capacity"] = {"offered_qps": capacity_rate, "served": srv.run(ctrace, CQ).summary(ctrace)}
+        del srv
+    return {"metric": "serving: queries/s and p50/p99 request latency, continuous batching",
+            "index": "gmm10k n=10000 d=128 (k=40 graph, e_o=10, e_i=30, path adjustment) + bf16 and FP8 copies",
+            "trace": {"seconds": seconds, "offered_qps": rate, "requests": len(trace), "queries": queries,
+                      "sizes": "log-uniform 1..256", "k": list(ks), "recall": list(recalls), "seed": synth.SEED_BASE + 5},
+            "runs": runs, "eps_e_s_table": tables, "same_alone_and_in_mix": same,
+            "admission": f"one {ws_mb} MB workspace pool; a batch takes what its grid needs"}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--seconds", type=float, default=60.0)
+    ap.add_argument("--rate", type=float, default=100_000.0, help="mean offered queries/s")
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--ws-mb", type=int, default=1024, help="device workspace budget over all slots (MB)")
+    ap.add_argument("--precisions", default="fp8,bf16", help="reduced precisions served (fp32 one-slot is the baseline)")
+    ap.add_argument("--e-s", type=int, default=10, help="first e_s tried per class (then 2x, 4x, every edge)")
+    ap.add_argument("--k-rerank", type=int, default=32, help="float32 rerank of max(k, this) in bf16 / fp8")
+    ap.add_argument("--capacity-rate", type=float, default=0.0, help="offered load of a short saturating run (0: skip)")
+    a = ap.parse_args()
+    line = serve_spec(a.seconds, a.rate, tuple(p for p in a.precisions.split(",") if p), a.slots, a.ws_mb, a.e_s,
+                      a.k_rerank, a.capacity_rate)
     print(json.dumps(line), flush=True)
 
 

@@ -56,3 +56,23 @@ def test_cpu_baseline_times_whole_passes(oracle_lib):
     r = bench.cpu_baseline(a, idx, X, Q, seeds, 0.1, min_wall=0.05, max_reps=3)
     assert r["kind"] == "oracle" and r["value"] > 0 and r["cores"] >= 1
     assert "pass(es) over all 40 queries" in r["sample"]
+
+
+def test_path_bytes_by_hand():
+    """Node 0 -> 1 (1.0), 2 (2.0); node 1 -> 2 (1.5); node 2 -> 0 (3.0), 1 (1.0),
+    with 4 output edges.  Edges shorter than their row's longest: (0,1) reads the
+    list of 1 (one entry) and (2,1) the list of 1: 2 entries of 8 bytes; plus
+    5 input + 4 output edges and two row-pointer arrays of 4 entries."""
+    ptr = torch.tensor([0, 2, 3, 5])
+    col = torch.tensor([1, 2, 2, 0, 1], dtype=torch.int32)
+    ln = torch.tensor([1.0, 2.0, 1.5, 3.0, 1.0])
+    assert bench.path_bytes(torch, ptr, col, ln, 4) == 2 * 8 + (5 + 4) * 8 + 2 * 4 * 8
+
+
+def test_parse_defaults_name_the_metric_workload():
+    a = bench.parse([])
+    assert (a.workload, a.n, a.nq, a.k, a.knn_k, a.e_o, a.e_i) == ("sift1m", 1_000_000, 10_000, 10, 100, 20, 60)
+    assert bench.parse(["--workload", "gist1m"]).nq == 1000
+    assert bench.parse(["--workload", "glove1m2"]).n == 1_200_000
+    c = bench.common_config(a, 0.1, 1)
+    assert c["workload"].startswith("sift-like n=1000000 d=128") and c["eps_fp32"] == 0.1

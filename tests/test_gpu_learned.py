@@ -50,7 +50,11 @@ def test_mlp_gradient_matches_oracle(onng):
     loss, G = onng.mlp_loss_grad(dev(P), dev(X), dev(T))
     o_loss, o_G = oracle.mlp_loss_grad(P.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
     assert abs(float(loss) - o_loss) <= 1e-4 * abs(o_loss)
-    np.testing.assert_allclose(host(G), o_G, rtol=1e-3, atol=1e-4 * np.abs(o_G).max())
+    g = host(G).astype(np.float64)
+    # within 1e-4 relative of the float64 gradient (as a vector), and element by
+    # element up to the float32 rounding of a 1000-term mean
+    assert np.linalg.norm(g - o_G) <= 1e-4 * np.linalg.norm(o_G)
+    np.testing.assert_allclose(g, o_G, rtol=1e-4, atol=1e-5 * np.abs(o_G).max())
 
 
 def test_mlp_adam_and_fused_training_match_oracle(onng):
@@ -171,14 +175,15 @@ def test_learned_search_trains_and_runs(onng, graph):
     assert (host(es_q) >= 6).all() and (host(es_q) <= 20).all()
 
 
-def test_learned_gain_over_fixed_policy(onng):
-    """What the trained network gains over the method without it, measured on
-    held-out queries at a target mean recall: the cost (distance computations per
-    query, probe included) of the network's policy for every shrinkage beta
-    against one global eps.  The chosen policy reaches the target and never costs
-    more than the fixed one (the fixed policy is a candidate).  The rank
-    correlation of the network's eps with the held-out label eps is printed: on
-    this workload it is near zero, and the choice falls back to the fixed eps."""
+def test_learned_against_fixed_and_eq1_policies(onng):
+    """What the trained network gains over the method without it, on held-out
+    queries at a target mean recall of 0.9: distance computations per query
+    (probe included) of the network's policy at each shrinkage beta, of one
+    global eps (the fixed policy) and of the paper's Eq. 1 policy (e_s tied to
+    eps by e_p = floor(10^(20 eps)) + 30, eps bisected).  Every reported policy
+    reaches the target; the table is printed.  The network's choice is the
+    cheapest of its rows; whether it beats the fixed policy is what the bench
+    reports, not something this test assumes."""
     from scipy.stats import spearmanr
 
     from paper_1810_07355_gb300 import learned
@@ -190,15 +195,35 @@ def test_learned_gain_over_fixed_policy(onng):
     gt, _ = onng.knn(dev(X), Qd, 10)
     seeds = onng.seeds_pivot(dev(X), Qd, 512, 10)
     tr, ho = slice(0, 800), slice(800, 1200)
+    target = 0.9
     pred, _ = learned.train(idx, Qd[tr], gt[tr], seeds[tr], 10, targets=(0.9, 1.0), h=4, steps=2000)
-    best, ybar, table = learned.select_shrinkage(pred, idx, Qd[ho], gt[ho], seeds[ho], 10, 0.9, 1.0,
+    best, ybar, table = learned.select_shrinkage(pred, idx, Qd[ho], gt[ho], seeds[ho], 10, target, 1.0,
                                                  es_options=(20,), precision=onng.PREC_FP32)
     fixed = [r for r in table if r["beta"] is None][0]
-    print("\nbeta  dc/query  recall")
+    net = [r for r in table if r["beta"] is not None and r["recall"] >= target - 1e-9]
+    # Eq. 1 on the same held-out queries
+    idx_csr = onng.Index(g[0], g[1], dev(X))
+
+    def eq1_run(eps):
+        ids, _, st = onng.search(idx_csr, Qd[ho], 10, learned.eq1_policy(eps), eps, seeds[ho])
+        return float(learned.recall_per_query(ids, gt[ho]).mean()), float(st[:, 0].float().mean())
+    lo, hi = 0.0, 0.2
+    if eq1_run(lo)[0] >= target:
+        hi = lo
+    for _ in range(14):
+        if hi == lo:
+            break
+        mid = 0.5 * (lo + hi)
+        lo, hi = (lo, mid) if eq1_run(mid)[0] >= target else (mid, hi)
+    eq1_rec, eq1_dc = eq1_run(hi)
+    print("\npolicy                      dc/query  recall")
     for r in table:
-        print(r["beta"], round(r["dc"], 1), round(r["recall"], 4))
-    assert best is not None and best["recall"] >= 0.9 - 1e-9
-    assert best["dc"] <= fixed["dc"] + 1e-9
+        print(f"{'fixed eps' if r['beta'] is None else 'network beta=' + str(r['beta']):26s}  {r['dc']:8.1f}  "
+              f"{r['recall']:.4f}")
+    print(f"{'Eq. 1 (eps=%.4f, e_s=%d)' % (hi, learned.eq1_policy(hi)):26s}  {eq1_dc:8.1f}  {eq1_rec:.4f}")
+    assert fixed["recall"] >= target - 1e-9 and eq1_rec >= target
+    assert net, "no network setting reaches the target"
+    assert best is not None and best["recall"] >= target - 1e-9
     # the network's own eps (beta = 1) against the held-out labels
     rec, cost = learned.sweep(idx, Qd[ho], gt[ho], seeds[ho], 10)
     eps_lab, _ = learned.labels_from_sweep(rec, cost, 1.0)

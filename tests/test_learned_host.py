@@ -46,3 +46,14 @@ def test_labels_from_sweep_and_lagrange_by_hand():
     # a high price prefers the cheapest cell
     e, s = learned.labels_lagrange(rec, cost, 0.1, eps_grid, es_grid)
     assert float(e[0]) == pytest.approx(0.0) and float(s[0]) == 8
+
+
+def test_eq1_policy_anchors():
+    """Eq. 1 with the paper's GIST setting e_0 = 30, w_e = 20, rounded down:
+    10^0 + 30, 10^1 + 30, 10^2 + 30."""
+    from paper_1810_07355_gb300 import learned
+    assert learned.eq1_policy(0.0) == 31
+    assert learned.eq1_policy(0.05) == 40
+    assert learned.eq1_policy(0.1) == 130
+    assert learned.eq1_policy(0.02) == 32  # floor(10^0.4) = 2
+    assert learned.eq1_policy(0.1, e0=10, we=10.0) == 20

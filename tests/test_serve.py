@@ -1,5 +1,6 @@
-"""Serving loop: request trace, class batching, and results that do not depend
-on what a request is batched with (continuous batching over several streams)."""
+"""Serving loop: request trace, class batching, workspace admission, the host
+watchdog, and results that do not depend on what a request is batched with
+(continuous batching over several streams)."""
 import numpy as np
 import pytest
 
@@ -33,6 +34,60 @@ def test_scheduler_batches_by_class_oldest_first():
     b = s.next_batch(4)  # a request larger than the capacity still goes alone
     assert b.reqs == [3] and b.nq == 9
     assert s.next_batch(10) is None and len(s) == 0
+
+
+def test_workspace_pool_first_fit_and_merge():
+    from paper_1810_07355_gb300.serve import WorkspacePool
+    p = WorkspacePool(4096, "cpu")
+    a = p.alloc(1000)  # rounded to 1024
+    b = p.alloc(1024)
+    c = p.alloc(2048)
+    assert (a, b, c) == (0, 1024, 2048) and p.alloc(1) is None and p.in_use() == 4096
+    p.free(b, 1024)
+    assert p.largest() == 1024 and p.alloc(2000) is None
+    p.free(a, 1000)  # merges with the free range after it
+    assert p.free_list == [(0, 2048)] and p.alloc(2048) == 0
+    p.free(0, 2048)
+    p.free(c, 2048)
+    assert p.free_list == [(0, 4096)] and p.in_use() == 0
+
+
+@pytest.mark.gpu
+def test_watchdog_stops_a_stalled_launch():
+    """A launch whose completion never shows on the host (a stall injected on the
+    host: its event reports unfinished forever) stops the loop with ServeTimeout
+    after the watchdog's limit; the device work itself completes normally."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import time
+
+    from paper_1810_07355_gb300 import onng
+    from paper_1810_07355_gb300.serve import Server, ServeTimeout
+    X, _ = synth.workload("gmm10k", n=3000)
+    trace = synth.request_trace(0.05, 20_000, seed=12)
+    _, Q = synth.workload("gmm10k", nq=int(trace["size"].sum()))
+    Xd = torch.from_numpy(X).cuda()
+    nbr, ln = onng.build_knng(Xd, 20)
+    g = onng.adjust_path(*onng.adjust_degree(nbr, ln, 10, 20))
+    index = onng.Index(g[0], g[1], Xd)
+    eps = {(k, r): 0.05 for k in (1, 10, 100) for r in (0.9, 0.95, 0.99)}
+    srv = Server(index, eps, 10, slots=2, ws_budget=64 << 20, timeout_s=0.5)
+
+    class Stalled:
+        def query(self):
+            return False
+
+    real = srv._launch
+
+    def stalled_launch(s, b, Q_, off, nbytes):
+        real(s, b, Q_, off, nbytes)
+        s.event.synchronize()
+        s.event = Stalled()
+    srv._launch = stalled_launch
+    t0 = time.perf_counter()
+    with pytest.raises(ServeTimeout):
+        srv.run(trace, Q)
+    assert 0.4 < time.perf_counter() - t0 < 5.0
 
 
 @pytest.mark.gpu
@@ -69,3 +124,16 @@ def test_serving_results_equal_alone_and_in_the_mix():
             kw = dict(precision=prec, k_rerank=max(20, k)) if prec else {}
             ids, dist, _ = onng.search(index, q, k, 10, eps[(k, float(r["recall"]))], s, **kw)
             assert np.array_equal(ids.cpu().numpy(), res.ids[rid]), rid
+        if prec == onng.PREC_FP32:
+            # served fp32 requests against Algorithm 1 in float64 (near-tie rule)
+            import oracle
+            from parity_helpers import assert_search_parity
+            ptr, col = g[0].cpu().numpy(), g[1].cpu().numpy()
+            for rid in range(0, len(trace), max(1, len(trace) // 12)):
+                r = trace[rid]
+                q = Q[r["first"]:r["first"] + r["size"]]
+                k = int(r["k"])
+                s = onng.seeds_pivot(Xd, torch.from_numpy(q).cuda(), 256, 10).cpu().numpy()
+                o = oracle.search(ptr, col, X, q, k, 10, np.float32(eps[(k, float(r["recall"]))]), s, margin=True)
+                st = np.zeros((len(q), 4), np.int64)
+                assert_search_parity(res.ids[rid], res.dist[rid], st, *o, X, q, min_tie_free=0.0, counts=False)
