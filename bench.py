@@ -177,6 +177,15 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+_T0 = time.perf_counter()
+
+
+def log(msg: str):
+    """Stage timestamps on stderr (the JSON line is the only stdout)."""
+    sys.stderr.write(f"[bench {time.perf_counter() - _T0:8.1f} s] {msg}\n")
+    sys.stderr.flush()
+
+
 def max_over_ranks(value: float, device) -> float:
     """The largest value over the ranks of the process group (the slowest rank sets
     the job's time); the value itself when there is no group or one rank."""
@@ -244,7 +253,7 @@ def build_index(onng, torch, Xd, a, peaks):
     torch.cuda.synchronize()
     t = [ev[i].elapsed_time(ev[i + 1]) / 1e3 for i in range(3)]
     idx = onng.Index(p[0], p[1], Xd, None, p[2])
-    if not a.no_adj:
+    if not a.no_adj and a.e_s > 0:
         idx.with_adjacency(a.e_s)
     idx.with_bf16()
     n, d = Xd.shape
@@ -271,12 +280,24 @@ def build_index(onng, torch, Xd, a, peaks):
     return idx, (nbr, ln), info
 
 
-def calibrate(run, gt, target, lo=0.0, hi=1.0, iters=12):
-    """Smallest eps (bisection) whose mean recall@k reaches the target."""
+EPS_CAP = 1.0  # r(1 + eps) at eps = 1 already admits nearly everything a query can reach
+
+
+def with_adj(idx, e_s):
+    """The index with its padded first-e_s adjacency table (every edge scanned: none)."""
+    return idx.with_adjacency(e_s) if e_s > 0 else idx
+
+
+def calibrate(run, gt, target, lo=0.0, hi=0.25, iters=12, cap=EPS_CAP):
+    """Smallest eps (bisection) whose mean recall@k reaches the target; `cap` if
+    even eps = cap does not reach it (the caller reports the recall reached)."""
+    hi = min(hi, cap)
     r_hi = recall_at(run(hi)[0], gt)
-    while r_hi < target and hi < 64:
-        lo, hi = hi, hi * 2
+    while r_hi < target and hi < cap:
+        lo, hi = hi, min(hi * 2, cap)
         r_hi = recall_at(run(hi)[0], gt)
+    if r_hi < target:
+        return hi
     if recall_at(run(lo)[0], gt) >= target:
         return lo
     for _ in range(iters):
@@ -293,7 +314,8 @@ def common_config(a, eps32, world):
     return {"workload": f"{a.desc}, {a.nq} queries, top-{a.k}", "knng_k": a.knn_k, "e_o": a.e_o, "e_i": a.e_i,
             "e_s": a.e_s, "seeds": f"{a.n_seed} nearest of {a.n_pivot} pivots", "eps_fp32": round(eps32, 5),
             "k_rerank": a.k_rerank, "l2": "inputs larger than L2 and L2 flushed between steps",
-            "adjacency": "csr" if a.no_adj else f"padded first {a.e_s}", "parallelism": f"replicas x{world}"}
+            "adjacency": "csr" if a.no_adj or a.e_s <= 0 else f"padded first {a.e_s}",
+            "parallelism": f"replicas x{world}"}
 
 
 def precision_error(torch, X, Q, ids, scale=None, codes=None):
@@ -336,9 +358,12 @@ def main():
         from paper_1810_07355_gb300 import serve
         print(json.dumps(serve.serve_spec(a.serve_seconds, a.serve_rate)), flush=True)
         return
+    log(f"generating {a.workload}")
     X, Q, Qtr = synth.workload(a.workload, n=a.n, nq=a.nq, train=a.ntrain)
     Xd, Qd, Qtrd = (torch.from_numpy(x).to(dev) for x in (X, Q, Qtr))
+    log("building the index")
     idx, knn_lists, build = build_index(onng, torch, Xd, a, peaks)
+    log(f"index built: {build['knng_s']} s kNN graph, {build['edges_path']} edges")
     gt, gt_len = onng.knn(Xd, Qd, a.k)
     seeds = onng.seeds_pivot(Xd, Qd, a.n_pivot, a.n_seed)
 
@@ -356,6 +381,7 @@ def main():
 
     forms = tuple(f for f in a.forms.split(",") if f)
     points = {"fp32": {"eps": round(eps32, 5), "e_s": a.e_s}}
+    log(f"fp32 eps {eps32:.5f}")
 
     def run16(eps):
         return onng.search(idx, Qd, a.k, a.e_s, eps, seeds, precision=onng.PREC_BF16, k_rerank=a.k_rerank)
@@ -378,12 +404,13 @@ def main():
         def run_eq1(eps):
             return onng.search(idx_csr, Qd, a.k, eq1_policy(eps), eps, seeds, precision=onng.PREC_BF16,
                                k_rerank=a.k_rerank)
-        eps_eq1 = calibrate(run_eq1, gt, a.target, hi=0.2)
+        eps_eq1 = calibrate(run_eq1, gt, a.target, hi=0.2, cap=0.2)
         es_eq1 = eq1_policy(eps_eq1)
         idx_eq1 = onng.Index(idx.row_ptr, idx.col, Xd, idx.X_bf16, idx.length)
         if not a.no_adj and es_eq1 <= 256:
             idx_eq1.with_adjacency(es_eq1)
         points["eq1"] = {"eps": round(eps_eq1, 5), "e_s": es_eq1, "policy": "e_p = floor(10^(20 eps)) + 30"}
+    log("reduced-precision forms calibrated")
     pred, t_pred, alpha = None, 1.0, 1.0
     learned_info = None
     if "learned" in forms:
@@ -464,6 +491,7 @@ def main():
             out = (ids, st)
         return step_ms, kern_ms, out
 
+    log("timing")
     for f in forms:
         timed(f, a.warmup)
     if world > 1:
@@ -518,6 +546,7 @@ def main():
     if "fp8" in forms:
         lowp["fp8"] = precision_error(torch, Xd, Qd, res["fp8"][2][0], idx.fp8_scale, idx.X_fp8)
 
+    log("timed region done")
     modes = None
     if a.build_modes and rank == 0:
         modes = build_modes(onng, torch, a, Xd, Qd, knn_lists, seeds, gt)
@@ -550,7 +579,8 @@ def main():
                         es = eq1_policy(eps) if f == "eq1" else a.e_s
                         ixc = idx_csr if f == "eq1" else ix
                         return onng.search(ixc, Qd, a.k, es, eps, s, precision=prec, k_rerank=kr)
-                    eps_t = calibrate(lambda e: runner(e, seeds), gt, t, hi=0.2 if f == "eq1" else 1.0)
+                    eps_t = calibrate(lambda e: runner(e, seeds), gt, t, hi=0.2 if f == "eq1" else 0.25,
+                                      cap=0.2 if f == "eq1" else EPS_CAP)
                     es_t = eq1_policy(eps_t) if f == "eq1" else a.e_s
                     if f == "eq1" and not a.no_adj and es_t <= 256:
                         ixt = onng.Index(idx.row_ptr, idx.col, Xd, idx.X_bf16, idx.length).with_adjacency(es_t)
@@ -579,6 +609,7 @@ def main():
     if not a.no_sweep and rank == 0:
         sweep = degree_sweep(onng, torch, a, Xd, Qd, knn_lists, seeds, gt, flush)
     e2e = end_to_end(onng, torch, a, idx, Q, head, pred, t_pred, alpha, eps32 if head == "fp32" else eps16, dev)
+    log("end to end done")
     cpu, parity = None, None
     if rank == 0 and world == 1:
         inputs = None if a.no_parity else ParityInputs(knn_lists, res["fp32"][2] if "fp32" in forms else None, gt,
@@ -641,7 +672,7 @@ def degree_sweep(onng, torch, a, Xd, Qd, knn_lists, seeds, gt, flush, steps=5):
     for e_o in (10, 20):
         for e_i in (40, 60, 100):
             g = onng.adjust_path(*onng.adjust_degree(nbr, ln, e_o, e_i))
-            idx = onng.Index(g[0], g[1], Xd).with_adjacency(a.e_s)
+            idx = with_adj(onng.Index(g[0], g[1], Xd), a.e_s)
             eps = calibrate(lambda e: onng.search(idx, Qd, a.k, a.e_s, e, seeds), gt, a.target)
             ms, ids, st = time_search(idx, a.k, eps)
             out.append({"e_o": e_o, "e_i": e_i, "k": a.k, "edges": int(g[0][-1]), "eps": round(eps, 5),
@@ -650,7 +681,7 @@ def degree_sweep(onng, torch, a, Xd, Qd, knn_lists, seeds, gt, flush, steps=5):
             del g, idx
     gt100, _ = onng.knn(Xd, Qd, 100)
     g = onng.adjust_path(*onng.adjust_degree(nbr, ln, a.e_o, a.e_i))
-    idx = onng.Index(g[0], g[1], Xd).with_adjacency(a.e_s)
+    idx = with_adj(onng.Index(g[0], g[1], Xd), a.e_s)
     eps = calibrate(lambda e: onng.search(idx, Qd, 100, a.e_s, e, seeds), gt100, a.target)
     ms, ids, st = time_search(idx, 100, eps)
     out.append({"e_o": a.e_o, "e_i": a.e_i, "k": 100, "edges": int(g[0][-1]), "eps": round(eps, 5),
@@ -678,7 +709,7 @@ def build_modes(onng, torch, a, Xd, Qd, knn_lists, seeds, gt):
         return r, e0.elapsed_time(e1) / 1e3
 
     def score(g):
-        idx = onng.Index(g[0], g[1], Xd).with_adjacency(a.e_s)
+        idx = with_adj(onng.Index(g[0], g[1], Xd), a.e_s)
         eps = calibrate(lambda e: onng.search(idx, Qd, a.k, a.e_s, e, seeds), gt, a.target)
         _, _, st = onng.search(idx, Qd, a.k, a.e_s, eps, seeds)
         return {"edges": int(g[0][-1]), "eps": round(eps, 5), "dc_per_query": round(float(st[:, 0].float().mean()), 1)}

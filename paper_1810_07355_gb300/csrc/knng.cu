@@ -536,6 +536,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int64_t self = (self_offset >= 0 && row_ok) ? self_offset + grow : -1;
         float thr = row_ok ? INFINITY : -INFINITY;
         s_xn[tid] = tid < n ? 0.5f * xn[tid] : INFINITY;
+        // the half norm this thread stages for the next tile, loaded one tile ahead
+        // so that its latency never sits in front of a barrier
+        float xn_next = TC_N + tid < n ? 0.5f * xn[TC_N + tid] : INFINITY;
         epi_sync();
         for (int64_t t = 0; t < tiles; ++t) {
             const int b = (int)(t & 1);
@@ -583,10 +586,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             tc_fence_before();
             mbar_arrive(&acce[b]);
-            // stage the next tile's half norms into the other half of s_xn
+            // stage the next tile's half norms into the other half of s_xn, and load
+            // those of the tile after it
+            s_xn[(b ^ 1) * TC_N + tid] = xn_next;
             {
-                const int64_t nc = (t + 1) * TC_N + tid;
-                s_xn[(b ^ 1) * TC_N + tid] = nc < n ? 0.5f * xn[nc] : INFINITY;
+                const int64_t nc = (t + 2) * TC_N + tid;
+                xn_next = nc < n ? 0.5f * xn[nc] : INFINITY;
             }
             epi_sync();
             const bool last = t + 1 == tiles;

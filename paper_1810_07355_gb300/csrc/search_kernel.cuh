@@ -4,25 +4,27 @@
 // host entry points.
 //
 // Per warp:
-//   - the visited set C, in shared memory, as an exact open-addressing hash
-//     (linear probing).  The paper's Set/IsSet table (Sec. 2.5) keeps the first
-//     id of a bucket inline and chains collisions; on the GPU a flat table probed
-//     by 32 lanes at once is cheaper.  Past half load, new ids go to a per-warp
-//     bitmap over all n ids in global memory (one atomicOr per id, no probing);
-//     the ids set there are logged and cleared when the query ends.
+//   - the visited set C, in shared memory, as buckets of 8 ids with two bucket
+//     choices per id (the paper's Set/IsSet table, Sec. 2.5, chains collisions
+//     off one inline id; here a batch of 32 ids reads both buckets of each id and
+//     claims free slots in lane order, with no probe loop).  An id that finds
+//     both of its buckets full moves the query to a per-warp bitmap over all n
+//     ids in global memory (one atomicOr per new id); the ids set there are
+//     logged and cleared when the query ends.
 //   - the candidate set S in three levels of (distance, id) keys: a sorted head
 //     of up to 32 keys in registers (one per lane: the pop is a shift, an
-//     insertion a ballot plus a shift), an unsorted overflow of up to 256 keys in
-//     shared memory whose keys are all >= every head key, and a per-warp spill
-//     pool in global memory whose keys are all >= tau > every key above it.  So
-//     the head's first key is the minimum of S; a level refills the one above
-//     only when that one runs empty.  An entry beyond r(1+eps) can never be
-//     expanded (r only shrinks, and popping it ends the search), so such entries
-//     are dropped whenever a level is rebuilt.  S stays exact.
+//     insertion a ballot plus a shift), an unsorted overflow in shared memory
+//     whose keys are all >= every head key, and a per-warp spill pool in global
+//     memory whose keys are all >= tau > every key above it.  So the head's
+//     first key is the minimum of S; a level refills the one above only when
+//     that one runs empty.  An entry beyond r(1+eps) can never be expanded (r
+//     only shrinks, and popping it ends the search), so such entries are
+//     dropped whenever a level is rebuilt.  S stays exact.
 //   - the result set R, in registers, as a sorted list of at most k keys.
-// The up-to-e_s neighbours of the expanded node are tested and their vectors
-// gathered together (coalesced 16-byte loads, several vectors in flight per
-// lane, one transposed butterfly reduction for all of them).  R then takes the k
+// The up-to-e_s neighbours of the expanded node are tested and the new ones'
+// vectors gathered together (their ids go to shared gather slots in lane order;
+// coalesced 16-byte loads, several vectors in flight per lane, one transposed
+// butterfly reduction for all of them).  R then takes the k
 // best of R and the batch, and S takes the batch members within the new
 // r(1+eps).  Applying a batch at once yields the same R, the same r after the
 // batch and, since S only loses entries that can never be expanded, the same
@@ -31,15 +33,18 @@
 // The node expanded next is known as soon as the batch's distances are: it is
 // the nearer of S's head and the batch's nearest member if that one will be
 // pushed (its distance is within the bound before the batch).  Its adjacency
-// row is loaded right then, so the load overlaps the R and S updates.
+// row is loaded right then, so the load overlaps the R and S updates, and once
+// the row is in, its neighbours' vectors are prefetched into L2.
 //
 // Adjacency is read from the CSR lists, or from an optional padded table
 // adj [n, width] (-1 padded) that holds each node's first `width` entries, which
 // saves the row-pointer indirection per expansion.
 //
-// Distances are squared float32 sums of (q - x)^2; bounds are compared in
-// double: d^2 <= r^2 (1 + eps)^2.  For integer-valued inputs with squared
-// distances below 2^24 every decision then equals the float64 algorithm's.
+// Distances are squared float32 sums of (q - x)^2; the bound r^2 (1 + eps)^2 is
+// formed in double whenever r changes and kept rounded down to float32, which
+// for a float32 d^2 decides d^2 <= r^2 (1 + eps)^2 exactly as the double
+// comparison does.  For integer-valued inputs with squared distances below 2^24
+// every decision then equals the float64 algorithm's.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -381,13 +386,17 @@ template <int V, class T, int HV, int KR> struct Warp {
     float r2;
     u64 tau;  // every key in the global pool is >= tau (kMaxKey when it is empty)
     double f2, bound2;
+    // bound2 rounded down to float32: for a float32 d^2, d^2 <= bound2 exactly when
+    // d^2 <= bnd (bound2 lies in [bnd, next float above bnd), so no float lies
+    // strictly between), which keeps the double comparison's decisions in float32
+    float bnd;
 
     __device__ Warp(WarpSmem<HV, kOvf> &s, const SearchArgs &args, const void *x, int ln, unsigned *gb, int *gl, u64 *gp)
         : sm(s), a(args), xs(x), lane(ln), gbits(gb), glog(gl), gpool(gp)
     {
     }
 
-    __device__ bool in_bound(u64 key) const { return (double)key_d2(key) <= bound2; }
+    __device__ bool in_bound(u64 key) const { return key_d2(key) <= bnd; }
 
     // ---------------------------------------------------------------- visited set
 
@@ -600,7 +609,11 @@ template <int V, class T, int HV, int KR> struct Warp {
         return true;
     }
 
-    __device__ void update_bound() { bound2 = (rset && !isinf(f2)) ? (double)r2 * f2 : INFINITY; }
+    __device__ void update_bound()
+    {
+        bound2 = (rset && !isinf(f2)) ? (double)r2 * f2 : INFINITY;
+        bnd = __double2float_rd(bound2);
+    }
 
     // ---------------------------------------------------------------- candidate pool
 
@@ -681,15 +694,19 @@ template <int V, class T, int HV, int KR> struct Warp {
 #pragma unroll
         for (int i = 0; i < 8; ++i)
             v[i] = kMaxKey;
+        u64 worst = kMaxKey;  // the 64th best so far: a chunk with nothing below it changes nothing
         for (int base = 0; base < ng; base += 128) {
 #pragma unroll
             for (int i = 2; i < 6; ++i) {
                 int e = base + (i - 2) * 32 + lane;
                 u64 kv = e < ng ? gpool[e] : kMaxKey;
-                v[i] = (kv != kMaxKey && in_bound(kv)) ? kv : kMaxKey;
+                v[i] = (kv < worst && in_bound(kv)) ? kv : kMaxKey;
             }
+            if (!__any_sync(FULL, v[2] != kMaxKey || v[3] != kMaxKey || v[4] != kMaxKey || v[5] != kMaxKey))
+                continue;
             v[6] = v[7] = kMaxKey;
             warp_bitonic_sort<8>(v, lane);
+            worst = __shfl_sync(FULL, v[1], 31);
         }
         const u64 kth = __shfl_sync(FULL, v[1], 31);
         sm.ovf[lane] = v[0];
@@ -870,7 +887,7 @@ template <int V, class T, int HV, int KR> struct Warp {
                                                                                                : 0xFFFFFFFFu);
             const u64 bmin = dmin == 0xFFFFFFFFu ? kMaxKey : ((u64)dmin << 32) | imin;
             const u64 top = __shfl_sync(FULL, head.v[0], 0);
-            const u64 next = ((double)key_d2(bmin) <= bound2 && bmin < top) ? bmin : top;
+            const u64 next = (key_d2(bmin) <= bnd && bmin < top) ? bmin : top;
             if (next != kMaxKey) {
                 pf_node = key_id(next);
                 pf_id = lane < es ? a.adj[(int64_t)pf_node * a.adj_w + lane] : -1;
@@ -893,7 +910,7 @@ template <int V, class T, int HV, int KR> struct Warp {
         }
         update_bound();
         // S <- S + batch members within r(1+eps)
-        pool_push(isnew && (double)d2 <= bound2, key);
+        pool_push(isnew && d2 <= bnd, key);
 #if ONNG_SEARCH_PREFETCH
         if (predict && pf_node >= 0 && pf_id >= 0) {
             // the row of the next node is in: its neighbours' vectors into L2
@@ -938,6 +955,7 @@ template <int V, class T, int HV, int KR> struct Warp {
         r2 = INFINITY;
         tau = kMaxKey;
         bound2 = INFINITY;
+        bnd = INFINITY;
         __syncwarp();
         for (int c0 = 0; c0 < a.n_seed; c0 += 32) {
             int id = -1;
@@ -958,13 +976,13 @@ template <int V, class T, int HV, int KR> struct Warp {
             }
             if (a.max_exp > 0 && nexp >= a.max_exp) {
                 // capped with a candidate still to expand (not merely pending termination)
-                capped = (double)key_d2(__shfl_sync(FULL, head.v[0], 0)) <= bound2;
+                capped = key_d2(__shfl_sync(FULL, head.v[0], 0)) <= bnd;
                 if (capped)
                     flags |= ONNG_FLAG_LIMIT;
                 break;
             }
             const u64 sk = pool_pop();
-            if ((double)key_d2(sk) > bound2)
+            if (key_d2(sk) > bnd)
                 break;
             ++nexp;
             const int s = key_id(sk);
