@@ -46,6 +46,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -64,6 +65,13 @@ NAMES = {"fp32": "plain fp32", "bf16": "fixed-eps bf16 + fp32 rerank", "fp8": "f
          "eq1": "Eq. 1 policy (e_s = 10^(20 eps) + 30), bf16 + fp32 rerank",
          "learned": "learned per-query eps/e_s, bf16 + fp32 rerank"}
 VEC_BYTES = {"fp32": 4, "bf16": 2, "fp8": 1, "eq1": 2, "learned": 2}
+# Pivots of the seed rule per workload: enough that every cluster of the
+# clustered stand-ins holds several (a cluster without one is reached only
+# through the graph's inter-cluster edges, which the kNN graph of well-separated
+# clusters barely has): 1,000 clusters -> 1,024; 500 -> 8,192 (about 16 each);
+# Zipf-sized clusters down to a few dozen points -> 16,384.
+PIVOTS = {"sift1m": 1024, "glove1m2": 16384, "gist1m": 8192}
+
 WORKLOADS = {  # name -> (base description, default queries)
     "sift1m": ("sift-like n={n} d=128 int0-255 fp32", 10_000),
     "glove1m2": ("text-like n={n} d=100 unit-norm fp32 (Zipf 1.1 over 2,000 directions)", 10_000),
@@ -86,7 +94,8 @@ def parse(argv=None):
     ap.add_argument("--e-o", type=int, default=20)
     ap.add_argument("--e-i", type=int, default=60)
     ap.add_argument("--e-s", type=int, default=20)
-    ap.add_argument("--n-pivot", type=int, default=1024)
+    ap.add_argument("--n-pivot", type=int, default=0,
+                    help="pivots of the seed rule (0: the workload's default, PIVOTS)")
     ap.add_argument("--n-seed", type=int, default=10)
     ap.add_argument("--target", type=float, default=0.95)
     ap.add_argument("--extra-targets", default="",
@@ -117,6 +126,8 @@ def parse(argv=None):
     ap.add_argument("--serve-rate", type=float, default=100_000.0)
     a = ap.parse_args(argv)
     desc, nq = WORKLOADS[a.workload]
+    if a.n_pivot <= 0:
+        a.n_pivot = PIVOTS[a.workload]
     if a.n is None:
         a.n = 1_200_000 if a.workload == "glove1m2" else 1_000_000
     if a.nq is None:
@@ -276,7 +287,13 @@ def build_index(onng, torch, Xd, a, peaks):
                          "frac": round(pb / t[2] / 1e9 / hbm, 4), "bytes": int(pb),
                          "note": "input + output CSR + the list of m for every edge (i,m) shorter than i's "
                                  "longest edge, 8 B an entry"}}}
-    del g
+    # Table 4's statistics of both graphs, and the 1-NNG's indegrees (Sec. 3.1)
+    keep = ("max_out", "max_in", "zero_in", "mean_out", "top5_out", "bottom5_in", "in_dist10")
+    one = onng.adjust_degree(nbr, ln, 1, 0)
+    info["graph_stats"] = {name: {key: round(v, 4) if isinstance(v, float) else v
+                                  for key, v in onng.graph_stats(*gr).items() if key in keep}
+                           for name, gr in (("degree", g), ("path", p), ("one_nn", one))}
+    del g, one
     return idx, (nbr, ln), info
 
 
@@ -796,6 +813,18 @@ class ParityInputs:
         self.knn, self.fp32, self.gt, self.gt_len, self.eps, self.seeds = knn_lists, fp32_out, gt, gt_len, eps, seeds
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), else the machine type."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
 def cpu_baseline(a, idx, X, Q, seeds, eps, min_wall: float = 1.5, max_reps: int = 5, parity=None):
     """The oracle's search (plain C, OpenMP over all host cores) on the whole query
     batch, repeated until min_wall seconds have passed (at most max_reps passes):
@@ -815,7 +844,15 @@ def cpu_baseline(a, idx, X, Q, seeds, eps, min_wall: float = 1.5, max_reps: int 
     dt = time.perf_counter() - t0
     base = {"value": round(done / dt, 1), "unit": "queries/s", "cores": cores, "kind": "oracle",
             "sample": f"{done // len(Q)} pass(es) over all {len(Q)} queries ({dt:.2f} s wall, about "
-                      f"{dt * cores:.0f} core-seconds), same index, seeds and fp32 eps (plain form)"}
+                      f"{dt * cores:.0f} core-seconds), same index, seeds and fp32 eps (plain form)",
+            "cpu_model": cpu_model()}
+    # the paper's own setting (Sec. 3): one thread
+    n1 = min(len(Q), 2000)
+    t1 = time.perf_counter()
+    oracle.search(ptr, col, X, Q[:n1], a.k, a.e_s, float(np.float32(eps)), s[:n1], threads=1)
+    dt1 = time.perf_counter() - t1
+    base["single_thread"] = {"value": round(n1 / dt1, 1), "unit": "queries/s", "cores": 1,
+                             "sample": f"the first {n1} queries once ({dt1:.2f} s)"}
     if parity is None:
         return base
     return {"baseline": base, "parity": parity_checks(a, idx, X, Q, o, parity, cores)}

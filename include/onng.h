@@ -45,6 +45,9 @@ enum onng_status {
 #define ONNG_FLAG_S_OVERFLOW 1u      /* candidate spill pool full: candidates dropped (see pool_cap) */
 #define ONNG_FLAG_VISIT_OVERFLOW 2u  /* reserved (the visited set cannot overflow) */
 #define ONNG_FLAG_LIMIT 4u           /* stopped by max_expansions with an in-bound candidate left */
+#define ONNG_FLAG_CHECK 8u           /* bounds-checked builds (-DONNG_CHECK, float32 search only): a graph
+                                        id outside [0, n), a row outside col or an overwritten shared-memory
+                                        canary was met; the access was skipped */
 
 const char *onng_last_error(void);
 int onng_version(void);
@@ -146,6 +149,57 @@ int onng_adjust_path_literal(const int64_t *row_ptr, const int32_t *col, const f
                              int64_t *row_ptr_out, int32_t *col_out, float *len_out, int64_t *nnz_host,
                              void *ws, size_t ws_bytes, onng_stream_t stream);
 
+/* ------------------------------------------------------------ graph statistics
+ * The graph statistics of Table 4 (Sec. 3.2), a diagnostic of a built graph
+ * (not on the search path).  With m = ceil(n / 20) (5 % of the nodes, at least
+ * one):
+ *   mean_out    nnz / n
+ *   top5_out    mean outdegree of the m nodes of largest outdegree
+ *   bottom5_in  mean indegree of the m nodes of smallest indegree
+ *   in_dist10   mean length over the edges of the transposed graph with every
+ *               node's incoming list cut to its 10 shortest (NaN without edges)
+ *   max_out, max_in, zero_in   largest outdegree and indegree, and the count of
+ *               nodes no edge reaches (the 1-NNG indegrees of Sec. 3.1, Fig. 1(b))
+ * row_ptr [n+1] must be a valid CSR (row_ptr[0] = 0, non-decreasing); col ids
+ * outside [0, n) give ONNG_E_INVAL (after the kernels ran, ignoring them).
+ * `out` is HOST memory; the call synchronises `stream`.  Degrees are counted as
+ * 32-bit; the length sum is accumulated in double in no fixed order. */
+typedef struct {
+    int64_t n, nnz, max_out, max_in, zero_in;
+    double mean_out, top5_out, bottom5_in, in_dist10;
+} onng_graph_stats_t;
+size_t onng_graph_stats_workspace_bytes(int64_t n, int64_t nnz);
+int onng_graph_stats(const int64_t *row_ptr, const int32_t *col, const float *len, int64_t n,
+                     onng_graph_stats_t *out, void *ws, size_t ws_bytes, onng_stream_t stream);
+
+/* ------------------------------------------------------------------ index files
+ * A built index written to disk and read back (the paper keeps its graphs as
+ * NGT index files and quotes their memory in Table 7; the format is this
+ * library's own).  Little-endian: a 64-byte header (magic "ONNGIDX\0", u32
+ * version 1, u32 flags with bit 0 = lengths present, i64 n, i32 d, u32 CRC-32 of
+ * the payload, i64 nnz, 24 zero bytes), then row_ptr [n+1] i64, col [nnz] i32,
+ * len [nnz] f32 (when present) and X [n, d] f32.  The CRC is the reflected
+ * CRC-32 of polynomial 0xEDB88320 (initial value and final xor 0xFFFFFFFF).
+ *   onng_index_save: writes the device arrays (len may be NULL) to `path`,
+ *                    replacing it; synchronises `stream`.
+ *   onng_index_check: reads the header and checks the payload size and CRC
+ *                    (host only, no CUDA call); optional outputs n, d, nnz and
+ *                    has_len (0 / 1).
+ *   onng_index_load: checks the file as onng_index_check does and that it holds
+ *                    the given n, d and nnz (and lengths when len != NULL), and
+ *                    only then copies it into the caller's device arrays;
+ *                    synchronises `stream`.
+ * A missing file, a wrong magic, version, size or CRC gives ONNG_E_INVAL with
+ * the reason in onng_last_error().
+ * onng_crc32: the CRC above over `len` bytes of host memory, continuing `crc`
+ * (0 to start). */
+int onng_index_save(const char *path, const int64_t *row_ptr, const int32_t *col, const float *len,
+                    const float *X, int64_t n, int32_t d, onng_stream_t stream);
+int onng_index_check(const char *path, int64_t *n, int32_t *d, int64_t *nnz, int32_t *has_len);
+int onng_index_load(const char *path, int64_t n, int32_t d, int64_t nnz, int64_t *row_ptr, int32_t *col,
+                    float *len, float *X, onng_stream_t stream);
+uint32_t onng_crc32(uint32_t crc, const void *data, size_t len);
+
 /* ---------------------------------------------------------------------- seeds
  * onng_seeds_random: the paper's random seeds (Sec. 3): n_seed distinct ids per
  * query, query q drawing from the SplitMix64 stream that starts at state
@@ -154,7 +208,8 @@ int onng_adjust_path_literal(const int64_t *row_ptr, const int32_t *col, const f
  *
  * onng_seeds_pivot: the n_seed nearest (distance, id) of the P = min(n_pivot, n)
  * pivots floor(t * n / P); stands in for the paper's vp-tree seeds (Sec. 2,
- * Table 5), which reach nodes roughly near the query.  n_seed <= 64.
+ * Table 5), which reach nodes roughly near the query.  n_seed <= 64; any
+ * n_pivot >= 1 (shared memory does not grow with it).
  */
 int onng_seeds_random(uint64_t global_seed, int64_t nq, int64_t n, int32_t n_seed, int32_t *out,
                       onng_stream_t stream);

@@ -90,6 +90,8 @@ def _load():
             lib.oracle_mlp_loss_grad.restype = dbl
             lib.oracle_adam_step.argtypes = [vp, vp, vp, vp, i64, i64, dbl, dbl, dbl, dbl]
             lib.oracle_adam_step.restype = None
+            lib.oracle_graph_stats.argtypes = [vp, vp, vp, i64, vp]
+            lib.oracle_graph_stats.restype = i32
             _lib = lib
     return _lib
 
@@ -343,3 +345,17 @@ def mlp_loss_grad(P, x, t):
 def adam_step(P, G, m, v, t: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
     """In-place Adam update of float64 arrays P, m, v."""
     _load().oracle_adam_step(_p(P), _p(_c(G, np.float64)), _p(m), _p(v), P.size, t, lr, beta1, beta2, eps)
+
+
+GRAPH_STATS = ("mean_out", "top5_out", "bottom5_in", "in_dist10", "max_out", "max_in", "zero_in")
+
+
+def graph_stats(ptr, col, length) -> dict:
+    """Table 4's graph statistics of a CSR graph (keys: GRAPH_STATS)."""
+    ptr = _c(ptr, np.int64)
+    col = _c(col, np.int32)
+    length = _c(length, np.float64)
+    out = np.empty(7, np.float64)
+    rc = _load().oracle_graph_stats(_p(ptr), _p(col), _p(length), ptr.shape[0] - 1, _p(out))
+    assert rc == 0
+    return dict(zip(GRAPH_STATS, out.tolist()))

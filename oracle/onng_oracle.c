@@ -34,6 +34,8 @@
  *                         e4m3 encode / decode it rests on)
  *   oracle_mlp_*          the per-query (eps, e_s) predictor network (no paper
  *                         counterpart; the paper's fixed policy is Eq. 1)
+ *   oracle_graph_stats    the graph statistics of Table 4 (Sec. 3.2) and the
+ *                         indegree extremes of Sec. 3.1
  */
 #include <math.h>
 #include <stdint.h>
@@ -1257,4 +1259,88 @@ void oracle_adam_step(double *P, const double *G, double *m, double *v, int64_t 
         double mh = m[i] / c1, vh = v[i] / c2;
         P[i] -= lr * mh / (sqrt(vh) + eps);
     }
+}
+
+/* ------------------------------------------------------ graph statistics
+ * Table 4 (Sec. 3.2).  With m = ceil(n / 20) (5 % of the nodes, at least one):
+ *   out[0] mean outdegree            nnz / n
+ *   out[1] mean top-5 % outdegree    mean outdegree of the m nodes of largest outdegree
+ *   out[2] mean bottom-5 % indegree  mean indegree of the m nodes of smallest indegree
+ *   out[3] mean indegree distance    mean length over the edges of the transposed
+ *                                    graph with every node's list cut to its 10
+ *                                    shortest (NaN without edges)
+ *   out[4] maximum outdegree, out[5] maximum indegree, out[6] nodes of indegree 0
+ * Plain definitions: degrees counted edge by edge, sorted with qsort. */
+static int cmp_i64_desc(const void *a, const void *b)
+{
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return (x < y) - (x > y);
+}
+
+static int cmp_dbl_asc(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+int oracle_graph_stats(const int64_t *ptr, const int32_t *col, const double *len, int64_t n, double *out)
+{
+    if (n < 1)
+        return ORACLE_E_INVAL;
+    const int64_t nnz = ptr[n];
+    int64_t *outdeg = malloc(sizeof(int64_t) * n), *indeg = calloc(n, sizeof(int64_t));
+    int64_t *inptr = calloc(n + 1, sizeof(int64_t)), *fill = calloc(n, sizeof(int64_t));
+    double *inlen = malloc(sizeof(double) * (nnz ? nnz : 1));
+    if (!outdeg || !indeg || !inptr || !fill || !inlen) {
+        free(outdeg), free(indeg), free(inptr), free(fill), free(inlen);
+        return ORACLE_E_NOMEM;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        outdeg[i] = ptr[i + 1] - ptr[i];
+        for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e)
+            indeg[col[e]] += 1;
+    }
+    int64_t max_out = 0, max_in = 0, zero_in = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (outdeg[i] > max_out)
+            max_out = outdeg[i];
+        if (indeg[i] > max_in)
+            max_in = indeg[i];
+        zero_in += indeg[i] == 0;
+    }
+    /* the transposed graph: incoming lengths of every node */
+    for (int64_t i = 0; i < n; ++i)
+        inptr[i + 1] = inptr[i] + indeg[i];
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
+            const int32_t j = col[e];
+            inlen[inptr[j] + fill[j]++] = len[e];
+        }
+    double dsum = 0.0;
+    int64_t dcnt = 0;
+    for (int64_t j = 0; j < n; ++j) {
+        const int64_t c = indeg[j];
+        qsort(inlen + inptr[j], (size_t)c, sizeof(double), cmp_dbl_asc);
+        for (int64_t t = 0; t < c && t < 10; ++t) {
+            dsum += inlen[inptr[j] + t];
+            ++dcnt;
+        }
+    }
+    const int64_t m = (n + 19) / 20;
+    qsort(outdeg, (size_t)n, sizeof(int64_t), cmp_i64_desc);
+    qsort(indeg, (size_t)n, sizeof(int64_t), cmp_i64_desc);
+    double top = 0.0, bottom = 0.0;
+    for (int64_t t = 0; t < m; ++t) {
+        top += (double)outdeg[t];
+        bottom += (double)indeg[n - 1 - t];
+    }
+    out[0] = (double)nnz / (double)n;
+    out[1] = top / (double)m;
+    out[2] = bottom / (double)m;
+    out[3] = dcnt ? dsum / (double)dcnt : NAN;
+    out[4] = (double)max_out;
+    out[5] = (double)max_in;
+    out[6] = (double)zero_in;
+    free(outdeg), free(indeg), free(inptr), free(fill), free(inlen);
+    return ORACLE_OK;
 }

@@ -34,6 +34,10 @@ VARIANTS = {
 }
 
 
+LIB_CHECK = os.path.join(HERE, "libonng_check.so")
+CHECK_FLAGS = ("-DONNG_CHECK",)
+
+
 def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
@@ -41,9 +45,12 @@ def _sources():
 def _units(extra):
     """(source, object, flags) of every object the library links."""
     out = []
+    checked = "-DONNG_CHECK" in extra
     for src in _sources():
         base = os.path.basename(src)[:-3]
         for tag, flags in VARIANTS.get(os.path.basename(src), [("", [])]):
+            if checked and tag.startswith(("t1", "t2")):
+                continue  # the bounds-checked build carries the float32 search only
             obj = os.path.join(BUILD, base + (f"_{tag}" if tag else "") + ".o")
             out.append((src, obj, flags + list(extra)))
     return out
@@ -91,6 +98,13 @@ def build(force: bool = False, verbose: bool = False, lib: str = LIB, extra=()) 
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, lib)
     return lib
+
+
+def build_checked(force: bool = False, verbose: bool = False) -> str:
+    """The bounds-checked library (-DONNG_CHECK): the search checks every id and
+    row it reads from the graph and canary words between the warps' shared
+    memory, flagging ONNG_FLAG_CHECK instead of reading out of bounds."""
+    return build(force=force, verbose=verbose, lib=LIB_CHECK, extra=CHECK_FLAGS)
 
 
 if __name__ == "__main__":

@@ -690,6 +690,7 @@ extern "C" int onng_adjust_degree_count(const int32_t *nbr, const float *len, in
                                         int32_t e_i, int64_t *row_ptr, int64_t *nnz_host, void *ws, size_t ws_bytes,
                                         onng_stream_t stream)
 {
+    ONNG_RANGE("onng_adjust_degree_count");
     int st = degree_args(nbr, len, n, k, e_o, e_i, ws, ws_bytes, "onng_adjust_degree_count");
     if (st)
         return st;
@@ -725,6 +726,7 @@ extern "C" int onng_adjust_degree(const int32_t *nbr, const float *len, int64_t 
                                   const int64_t *row_ptr, int32_t *col, float *len_out, void *ws, size_t ws_bytes,
                                   onng_stream_t stream)
 {
+    ONNG_RANGE("onng_adjust_degree");
     int st = degree_args(nbr, len, n, k, e_o, e_i, ws, ws_bytes, "onng_adjust_degree");
     if (st)
         return st;
@@ -822,6 +824,7 @@ extern "C" int onng_adjust_degree_sac_count(const int32_t *nbr, const float *len
                                             int32_t e_i, int64_t *row_ptr, int64_t *nnz_host, void *ws,
                                             size_t ws_bytes, onng_stream_t stream)
 {
+    ONNG_RANGE("onng_adjust_degree_sac_count");
     ONNG_REQUIRE(n >= 0 && n <= INT32_MAX && k >= 1 && e_o >= 0 && e_i >= 0, ONNG_E_INVAL,
                  "onng_adjust_degree_sac_count: bad sizes");
     ONNG_REQUIRE(n == 0 || (nbr && len), ONNG_E_INVAL, "onng_adjust_degree_sac_count: NULL input");
@@ -857,6 +860,7 @@ extern "C" int onng_adjust_degree_sac(const int32_t *nbr, const float *len, int6
                                       int32_t e_i, const int64_t *row_ptr, int32_t *col, float *len_out, void *ws,
                                       size_t ws_bytes, onng_stream_t stream)
 {
+    ONNG_RANGE("onng_adjust_degree_sac");
     ONNG_REQUIRE(n >= 0 && n <= INT32_MAX && k >= 1 && e_o >= 0 && e_i >= 0, ONNG_E_INVAL,
                  "onng_adjust_degree_sac: bad sizes");
     ONNG_REQUIRE(n == 0 || (nbr && len), ONNG_E_INVAL, "onng_adjust_degree_sac: NULL input");
@@ -905,6 +909,7 @@ extern "C" int onng_adjust_path_literal(const int64_t *row_ptr, const int32_t *c
                                         int64_t *row_ptr_out, int32_t *col_out, float *len_out, int64_t *nnz_host,
                                         void *ws, size_t ws_bytes, onng_stream_t stream)
 {
+    ONNG_RANGE("onng_adjust_path_literal");
     // ids are sorted as (id << 32 | position) keys below the sorters' padding key
     ONNG_REQUIRE(n >= 0 && n < 0x7F800000LL, ONNG_E_INVAL, "onng_adjust_path_literal: bad n");
     ONNG_REQUIRE(row_ptr && row_ptr_out, ONNG_E_INVAL, "onng_adjust_path_literal: NULL row_ptr");
@@ -1035,6 +1040,7 @@ extern "C" int onng_adjust_path(const int64_t *row_ptr, const int32_t *col, cons
                                 int64_t *row_ptr_out, int32_t *col_out, float *len_out, int64_t *nnz_host,
                                 int32_t *removed_by, void *ws, size_t ws_bytes, onng_stream_t stream)
 {
+    ONNG_RANGE("onng_adjust_path");
     ONNG_REQUIRE(n >= 0 && n <= INT32_MAX, ONNG_E_INVAL, "onng_adjust_path: bad n");
     ONNG_REQUIRE(row_ptr && row_ptr_out, ONNG_E_INVAL, "onng_adjust_path: NULL row_ptr");
     cudaStream_t s = to_cuda(stream);

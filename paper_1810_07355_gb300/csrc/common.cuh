@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <stdio.h>
 
@@ -36,6 +37,16 @@ inline int check_launch(const char *what)
         if (!(cond))                                        \
             return ::onng::set_error(status, __VA_ARGS__);  \
     } while (0)
+
+// A named host range around an entry point for timeline tools (NVTX); costs a
+// branch when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define ONNG_RANGE(name) ::onng::NvtxRange onng_range_(name)
 
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 

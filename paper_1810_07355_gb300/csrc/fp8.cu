@@ -51,6 +51,7 @@ using namespace onng;
 
 extern "C" int onng_to_fp8(const float *X, int64_t n, int32_t d, float *scale, uint8_t *out, onng_stream_t stream)
 {
+    ONNG_RANGE("onng_to_fp8");
     ONNG_REQUIRE(n >= 0 && d > 0, ONNG_E_INVAL, "onng_to_fp8: bad sizes");
     ONNG_REQUIRE(X && scale && out, ONNG_E_INVAL, "onng_to_fp8: NULL pointer");
     cudaStream_t s = to_cuda(stream);

@@ -768,6 +768,7 @@ extern "C" size_t onng_knn_workspace_bytes(int64_t n, int32_t d, int64_t nq, int
 extern "C" int onng_knn(const float *X, int64_t n, int32_t d, const float *Q, int64_t nq, int32_t k,
                         int64_t self_offset, int32_t *nbr, float *len, void *ws, size_t ws_bytes, onng_stream_t stream)
 {
+    ONNG_RANGE("onng_knn");
     ONNG_REQUIRE(n >= 0 && nq >= 0 && n <= INT32_MAX, ONNG_E_INVAL, "onng_knn: bad sizes");
     ONNG_REQUIRE(d > 0 && d % 4 == 0, ONNG_E_UNSUPPORTED, "onng_knn: d must be a positive multiple of 4");
     ONNG_REQUIRE(k >= 1, ONNG_E_INVAL, "onng_knn: k must be >= 1");
@@ -818,6 +819,7 @@ extern "C" int onng_knn(const float *X, int64_t n, int32_t d, const float *Q, in
 extern "C" int onng_build_knng(const float *X, int64_t n, int32_t d, int32_t k, int32_t *nbr, float *len, void *ws,
                                size_t ws_bytes, onng_stream_t stream)
 {
+    ONNG_RANGE("onng_build_knng");
     ONNG_REQUIRE(k <= n - 1 || n == 0, ONNG_E_INVAL, "onng_build_knng: k must be <= n - 1");
     return onng_knn(X, n, d, X, n, k, 0, nbr, len, ws, ws_bytes, stream);
 }

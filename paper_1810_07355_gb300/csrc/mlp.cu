@@ -487,6 +487,7 @@ extern "C" int onng_mlp_nparam(void) { return NP; }
 
 extern "C" int onng_mlp_forward(const float *P, const float *X, int64_t B, float *Y, onng_stream_t stream)
 {
+    ONNG_RANGE("onng_mlp_forward");
     ONNG_REQUIRE(B >= 0, ONNG_E_INVAL, "onng_mlp_forward: negative batch");
     if (B == 0)
         return ONNG_OK;
@@ -502,6 +503,7 @@ extern "C" int onng_mlp_forward(const float *P, const float *X, int64_t B, float
 extern "C" int onng_mlp_loss_grad(const float *P, const float *X, const float *T, int64_t B, float *G, float *loss,
                                   onng_stream_t stream)
 {
+    ONNG_RANGE("onng_mlp_loss_grad");
     ONNG_REQUIRE(B >= 1, ONNG_E_INVAL, "onng_mlp_loss_grad: empty batch");
     ONNG_REQUIRE(P && X && T && G && loss, ONNG_E_INVAL, "onng_mlp_loss_grad: NULL pointer");
     cudaStream_t s = to_cuda(stream);
@@ -518,6 +520,7 @@ extern "C" int onng_mlp_loss_grad(const float *P, const float *X, const float *T
 extern "C" int onng_mlp_adam(float *P, const float *G, float *M, float *V, int64_t t, float lr, float beta1,
                              float beta2, float eps, onng_stream_t stream)
 {
+    ONNG_RANGE("onng_mlp_adam");
     ONNG_REQUIRE(t >= 1 && lr > 0.f, ONNG_E_INVAL, "onng_mlp_adam: bad step or rate");
     ONNG_REQUIRE(P && G && M && V, ONNG_E_INVAL, "onng_mlp_adam: NULL pointer");
     mlp_adam_kernel<<<(NP + 255) / 256, 256, 0, to_cuda(stream)>>>(P, G, M, V, t, lr, beta1, beta2, eps);
@@ -527,6 +530,7 @@ extern "C" int onng_mlp_adam(float *P, const float *G, float *M, float *V, int64
 extern "C" int onng_mlp_train(float *P, float *M, float *V, const float *X, const float *T, int64_t N, int32_t batch,
                               int64_t steps, int64_t t0, float lr, float *G, float *losses, onng_stream_t stream)
 {
+    ONNG_RANGE("onng_mlp_train");
     (void)G;
     ONNG_REQUIRE(N >= 1 && batch >= 1 && steps >= 0 && t0 >= 0 && lr > 0.f, ONNG_E_INVAL, "onng_mlp_train: bad sizes");
     ONNG_REQUIRE(batch <= kTrainMaxB, ONNG_E_UNSUPPORTED, "onng_mlp_train: batch must be <= %d", kTrainMaxB);
@@ -545,6 +549,7 @@ extern "C" int onng_mlp_train(float *P, float *M, float *V, const float *X, cons
 extern "C" int onng_mlp_predict(const float *P, const float *X, int64_t B, float alpha, int32_t es_min, int32_t es_max,
                                 float *eps_out, int32_t *es_out, onng_stream_t stream)
 {
+    ONNG_RANGE("onng_mlp_predict");
     ONNG_REQUIRE(B >= 0 && es_min >= 1 && es_max >= es_min && alpha >= 0.f, ONNG_E_INVAL, "onng_mlp_predict: bad args");
     if (B == 0)
         return ONNG_OK;

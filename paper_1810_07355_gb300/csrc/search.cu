@@ -33,19 +33,27 @@ template <class T, int V> Launch pick_kr(int k)
 
 template <class T> Launch pick_v(int d, int k)
 {
-    const int V = (d + 127) / 128;
-    if (V <= 1)
-        return pick_kr<T, 1>(k);
-    if constexpr (ONNG_SEARCH_MAXV >= 2)
-        if (V <= 2)
-            return pick_kr<T, 2>(k);
-    if constexpr (ONNG_SEARCH_MAXV >= 4)
-        if (V <= 4)
-            return pick_kr<T, 4>(k);
-    if constexpr (ONNG_SEARCH_MAXV >= 8)
-        if (V <= 8)
-            return pick_kr<T, 8>(k);
-    return {nullptr, 0};
+#ifdef ONNG_CHECK
+    // the bounds-checked build carries the float32 kernels only
+    if constexpr (!std::is_same<T, float>::value) {
+        return {nullptr, 0};
+    } else
+#endif
+    {
+        const int V = (d + 127) / 128;
+        if (V <= 1)
+            return pick_kr<T, 1>(k);
+        if constexpr (ONNG_SEARCH_MAXV >= 2)
+            if (V <= 2)
+                return pick_kr<T, 2>(k);
+        if constexpr (ONNG_SEARCH_MAXV >= 4)
+            if (V <= 4)
+                return pick_kr<T, 4>(k);
+        if constexpr (ONNG_SEARCH_MAXV >= 8)
+            if (V <= 8)
+                return pick_kr<T, 8>(k);
+        return {nullptr, 0};
+    }
 }
 
 int resident_blocks(const Launch &L, int *per_sm)
@@ -94,6 +102,7 @@ extern "C" size_t onng_search_workspace_bytes(int64_t nq, const onng_index *idx,
 extern "C" int onng_pad_adjacency(const int64_t *row_ptr, const int32_t *col, int64_t n, int32_t width, int32_t *adj,
                                   onng_stream_t stream)
 {
+    ONNG_RANGE("onng_pad_adjacency");
     ONNG_REQUIRE(n >= 0 && width >= 1, ONNG_E_INVAL, "onng_pad_adjacency: bad sizes");
     if (n == 0)
         return ONNG_OK;
@@ -205,6 +214,7 @@ extern "C" int onng_search(const onng_index *idx, const float *Q, int64_t nq, co
                            int32_t *out_ids, float *out_dist, int32_t *stats, void *ws, size_t ws_bytes,
                            onng_stream_t stream)
 {
+    ONNG_RANGE("onng_search");
     return search_impl(idx, Q, nq, p, seeds, n_seed, eps_q, es_q, out_ids, out_dist, stats, nullptr, 0.f, ws,
                        ws_bytes, stream);
 }
@@ -213,6 +223,7 @@ extern "C" int onng_search_probe(const onng_index *idx, const float *Q, int64_t 
                                  const int32_t *seeds, int32_t n_seed, float target, float *features, int32_t *stats,
                                  void *ws, size_t ws_bytes, onng_stream_t stream)
 {
+    ONNG_RANGE("onng_search_probe");
     ONNG_REQUIRE(p && p->max_expansions >= 1, ONNG_E_INVAL, "onng_search_probe: max_expansions must be >= 1");
     ONNG_REQUIRE(features || nq == 0, ONNG_E_INVAL, "onng_search_probe: NULL features");
     return search_impl(idx, Q, nq, p, seeds, n_seed, nullptr, nullptr, nullptr, nullptr, stats, features, target, ws,
@@ -264,6 +275,7 @@ extern "C" int onng_search_noalloc(const onng_index *idx, const float *Q, int64_
                                    const int32_t *seeds, int32_t n_seed, const float *eps_q, const int32_t *es_q,
                                    int32_t *out_ids, float *out_dist, int32_t *stats, onng_stream_t stream)
 {
+    ONNG_RANGE("onng_search_noalloc");
     ONNG_REQUIRE(idx && p, ONNG_E_INVAL, "onng_search_noalloc: NULL index or params");
     ONNG_REQUIRE(idx->n > 0 && idx->n <= INT32_MAX, ONNG_E_INVAL, "onng_search_noalloc: bad index size");
     // one CTA's share: the query counter's slot plus kWarpsPerCta per-warp slots

@@ -185,7 +185,14 @@ template <int HV, int OVF> struct WarpSmem {
     int vis[HV];
     u64 ovf[OVF];
     int slot[32];  // ids of a batch's new nodes in lane order (gather slots)
+#ifdef ONNG_CHECK
+    unsigned canary[4];  // between this warp's arrays and the next warp's
+#endif
 };
+
+#ifdef ONNG_CHECK
+constexpr unsigned kCanary = 0x0C4A7A10u;
+#endif
 
 __host__ __device__ constexpr int log2i(int v) { return v <= 1 ? 0 : 1 + log2i(v >> 1); }
 
@@ -379,6 +386,9 @@ template <int V, class T, int HV, int KR> struct Warp {
     int nh, no, ng, cnt, ndc, nexp, nvis, nlog, kk, nscan, es;
     int pf_node, pf_id;  // adjacency row already loaded for the next expansion
     unsigned flags;
+#ifdef ONNG_CHECK
+    int64_t nnz_chk;  // row_ptr[n]: every row must lie inside col
+#endif
     bool spill, rset, stop, padded, capped;
     int seed_cnt, rins;  // probe features: seeds evaluated, result insertions
     float seed_sum;
@@ -607,6 +617,21 @@ template <int V, class T, int HV, int KR> struct Warp {
         res.insert_at(pos, key, lane, kk);
         cnt = min(cnt + 1, kk);
         return true;
+    }
+
+    // Bounds-checked builds (-DONNG_CHECK): an id read from the graph outside
+    // [-1, n) becomes -1 (no access) and flags the query ONNG_FLAG_CHECK.  Called
+    // by the whole warp.  Other builds trust the graph.
+    __device__ __forceinline__ int graph_id(int id)
+    {
+#ifdef ONNG_CHECK
+        const bool bad = id < -1 || id >= a.n;
+        if (__any_sync(FULL, bad))
+            flags |= ONNG_FLAG_CHECK;
+        return bad ? -1 : id;
+#else
+        return id;
+#endif
     }
 
     __device__ void update_bound()
@@ -890,7 +915,7 @@ template <int V, class T, int HV, int KR> struct Warp {
             const u64 next = (key_d2(bmin) <= bnd && bmin < top) ? bmin : top;
             if (next != kMaxKey) {
                 pf_node = key_id(next);
-                pf_id = lane < es ? a.adj[(int64_t)pf_node * a.adj_w + lane] : -1;
+                pf_id = graph_id(lane < es ? a.adj[(int64_t)pf_node * a.adj_w + lane] : -1);
             }
         }
         // R <- the best kk of R and the batch
@@ -949,6 +974,9 @@ template <int V, class T, int HV, int KR> struct Warp {
         pf_node = -1;
         kk = a.k;
         flags = 0;
+#ifdef ONNG_CHECK
+        nnz_chk = a.row_ptr[a.n];
+#endif
         spill = rset = stop = capped = false;
         seed_cnt = rins = 0;
         seed_sum = 0.f;
@@ -987,13 +1015,13 @@ template <int V, class T, int HV, int KR> struct Warp {
             ++nexp;
             const int s = key_id(sk);
             if (predict) {
-                const int id = s == pf_node ? pf_id : (lane < es ? a.adj[(int64_t)s * a.adj_w + lane] : -1);
+                const int id = s == pf_node ? pf_id : graph_id(lane < es ? a.adj[(int64_t)s * a.adj_w + lane] : -1);
                 pf_node = -1;
                 nscan += __popc(__ballot_sync(FULL, id >= 0));
                 batch(id, false, true);
             } else if (padded) {
                 for (int c0 = 0; c0 < es && !stop; c0 += 32) {
-                    const int id = c0 + lane < es ? a.adj[(int64_t)s * a.adj_w + c0 + lane] : -1;
+                    const int id = graph_id(c0 + lane < es ? a.adj[(int64_t)s * a.adj_w + c0 + lane] : -1);
                     const unsigned got = __ballot_sync(FULL, id >= 0);
                     if (!got)
                         break;
@@ -1002,11 +1030,17 @@ template <int V, class T, int HV, int KR> struct Warp {
                 }
             } else {
                 const int64_t beg = a.row_ptr[s];
-                const int64_t deg = a.row_ptr[s + 1] - beg;
+                int64_t deg = a.row_ptr[s + 1] - beg;
+#ifdef ONNG_CHECK
+                if (beg < 0 || deg < 0 || beg + deg > nnz_chk) {
+                    flags |= ONNG_FLAG_CHECK;
+                    deg = 0;
+                }
+#endif
                 const int m = deg < (int64_t)es ? (int)deg : es;
                 nscan += m;
                 for (int c0 = 0; c0 < m && !stop; c0 += 32) {
-                    int id = c0 + lane < m ? a.col[beg + c0 + lane] : -1;
+                    int id = graph_id(c0 + lane < m ? a.col[beg + c0 + lane] : -1);
                     batch(id, false, false);
                 }
             }
@@ -1088,6 +1122,10 @@ template <int V, class T, int HV, int KR> struct Warp {
                 a.out_dist[q * k + e] = e < cnt ? sqrtf(key_d2(res.v[i])) : INFINITY;
             }
         }
+#ifdef ONNG_CHECK
+        if (__any_sync(FULL, lane < 4 && sm.canary[lane] != kCanary + lane))
+            flags |= ONNG_FLAG_CHECK;
+#endif
         if (a.stats && lane == 0) {
             a.stats[q * 4 + 0] = ndc;
             a.stats[q * 4 + 1] = nexp;
@@ -1117,6 +1155,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, min_blocks<T>(V, KR)) searc
                                                               : static_cast<const void *>(a.X8);
     Warp<V, T, HV, KR> w(smem[warp], a, xs, lane, a.gbits + slot * a.bits_words, a.glog + slot * kVisitLog,
                          a.gpool + slot * a.gpool_cap);
+#ifdef ONNG_CHECK
+    if (lane < 4)
+        smem[warp].canary[lane] = kCanary + lane;
+    __syncwarp();
+#endif
     for (;;) {
         int q = 0;
         if (lane == 0)

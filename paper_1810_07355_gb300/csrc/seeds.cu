@@ -10,12 +10,12 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "warp_sort.cuh"
 
 namespace onng {
 namespace {
 
 constexpr int kMaxSeed = 64;
-constexpr int kMaxPivot = 2048;
 
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long &state)
 {
@@ -60,19 +60,22 @@ __global__ void seeds_random_kernel(unsigned long long global_seed, int64_t nq, 
 // tiles of kPivT: each tile (in chunks of kPivD coordinates) and the CTA's
 // queries are staged in shared memory, and thread (i, j) accumulates the
 // squared distances of query i to pivots j, j + 16, j + 32, j + 48 of the tile
-// by direct difference in float32.  All P distances of a query stay in shared
-// memory; then one warp per query takes n_seed rounds of an argmin over
-// (distance, pivot index).  Every pivot row is read once per CTA instead of once
-// per query.
+// by direct difference in float32.  After each tile a warp per query merges the
+// tile's 64 (distance, pivot index) keys into the query's sorted list of its 64
+// best so far (a bitonic sort of 128 keys, skipped when no key of the tile beats
+// the list's n_seed-th).  Every pivot row is read once per CTA instead of once
+// per query, and shared memory does not grow with the pivot count.
 constexpr int kPivQ = 16;
 constexpr int kPivT = 64;
 constexpr int kPivD = 128;
 constexpr int kPivThreads = 256;
 constexpr int kPivRow = kPivD + 4;  // padded tile row: conflict-free 16-byte reads
+constexpr unsigned long long kNoKey = ~0ull;
 
-size_t pivot_smem_bytes(int P)
+size_t pivot_smem_bytes()
 {
-    return sizeof(float) * ((size_t)kPivQ * kPivD + (size_t)kPivT * kPivRow + (size_t)kPivQ * P);
+    return sizeof(float) * ((size_t)kPivQ * kPivD + (size_t)kPivT * kPivRow + (size_t)kPivQ * kPivT) +
+           sizeof(unsigned long long) * (size_t)kPivQ * kMaxSeed;
 }
 
 __global__ void __launch_bounds__(kPivThreads)
@@ -80,13 +83,18 @@ __global__ void __launch_bounds__(kPivThreads)
                        int n_seed, int32_t *__restrict__ out)
 {
     extern __shared__ __align__(16) float psm[];
-    float *qs = psm;                      // [kPivQ][kPivD]
-    float *ts = qs + kPivQ * kPivD;       // [kPivT][kPivRow]
-    float *dist = ts + kPivT * kPivRow;   // [kPivQ][P]
+    float *qs = psm;                     // [kPivQ][kPivD]
+    float *ts = qs + kPivQ * kPivD;      // [kPivT][kPivRow]
+    float *dist = ts + kPivT * kPivRow;  // [kPivQ][kPivT]: the tile's squared distances
+    unsigned long long *best = reinterpret_cast<unsigned long long *>(dist + kPivQ * kPivT);  // [kPivQ][kMaxSeed]
     const int tid = threadIdx.x;
     const int qi = tid >> 4, pj = tid & 15;
+    const int warp = tid >> 5, lane = tid & 31;
     const int64_t q0 = (int64_t)blockIdx.x * kPivQ;
     const int d4 = d >> 2;
+    const int m = n_seed < P ? n_seed : P;
+    for (int e = tid; e < kPivQ * kMaxSeed; e += kPivThreads)
+        best[e] = kNoKey;
     for (int t0 = 0; t0 < P; t0 += kPivT) {
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
         for (int c0 = 0; c0 < d4; c0 += kPivD / 4) {
@@ -114,66 +122,54 @@ __global__ void __launch_bounds__(kPivThreads)
             for (int c = 0; c < kPivD / 4; ++c) {
                 const float4 a = qr[c];
 #pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    const float4 b = reinterpret_cast<const float4 *>(ts + (pj + 16 * m) * kPivRow)[c];
+                for (int mm = 0; mm < 4; ++mm) {
+                    const float4 b = reinterpret_cast<const float4 *>(ts + (pj + 16 * mm) * kPivRow)[c];
                     float u = a.x - b.x;
-                    acc[m] = fmaf(u, u, acc[m]);
+                    acc[mm] = fmaf(u, u, acc[mm]);
                     u = a.y - b.y;
-                    acc[m] = fmaf(u, u, acc[m]);
+                    acc[mm] = fmaf(u, u, acc[mm]);
                     u = a.z - b.z;
-                    acc[m] = fmaf(u, u, acc[m]);
+                    acc[mm] = fmaf(u, u, acc[mm]);
                     u = a.w - b.w;
-                    acc[m] = fmaf(u, u, acc[m]);
+                    acc[mm] = fmaf(u, u, acc[mm]);
                 }
             }
         }
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const int t = t0 + pj + 16 * m;
-            if (t < P)
-                dist[qi * P + t] = acc[m];
+        for (int mm = 0; mm < 4; ++mm)
+            dist[qi * kPivT + pj + 16 * mm] = acc[mm];
+        __syncthreads();
+        // merge the tile into each query's best list: keys (distance bits, pivot
+        // index) order as (distance, index) for non-negative distances; NaN
+        // distances (non-finite input) are never taken
+        for (int i = warp; i < kPivQ; i += kPivThreads / 32) {
+            unsigned long long v[4];
+            unsigned long long *bl = best + i * kMaxSeed;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int t = t0 + lane + 32 * h;
+                const float dv = dist[i * kPivT + lane + 32 * h];
+                v[2 + h] = (t < P && !isnan(dv)) ? pack_key(dv, t) : kNoKey;
+                v[h] = bl[lane + 32 * h];
+            }
+            const unsigned long long kth = bl[m - 1];
+            if (__any_sync(0xffffffffu, v[2] < kth || v[3] < kth)) {
+                warp_bitonic_sort<4>(v, lane);
+                bl[lane] = v[0];
+                bl[32 + lane] = v[1];
+            }
+            __syncwarp();
         }
     }
     __syncthreads();
-    const int warp = tid >> 5, lane = tid & 31;
-    const int m = n_seed < P ? n_seed : P;
     for (int i = warp; i < kPivQ; i += kPivThreads / 32) {
         const int64_t q = q0 + i;
         if (q >= nq)
             break;
-        float *dw = dist + i * P;
-        for (int r = 0; r < m; ++r) {
-            float bd = INFINITY;
-            int bt = INT_MAX;
-            for (int t = lane; t < P; t += 32) {
-                const float v = dw[t];
-                if (v < bd || (v == bd && t < bt)) {
-                    bd = v;
-                    bt = t;
-                }
-            }
-#pragma unroll
-            for (int off = 16; off >= 1; off >>= 1) {
-                const float od = __shfl_xor_sync(0xffffffffu, bd, off);
-                const int ot = __shfl_xor_sync(0xffffffffu, bt, off);
-                if (od < bd || (od == bd && ot < bt)) {
-                    bd = od;
-                    bt = ot;
-                }
-            }
-            if (bt >= P) {  // only NaN distances left (non-finite input): no further seeds
-                for (int e = r + lane; e < n_seed; e += 32)
-                    out[q * n_seed + e] = -1;
-                break;
-            }
-            if (lane == 0) {
-                out[q * n_seed + r] = (int32_t)((int64_t)bt * n / P);
-                dw[bt] = __int_as_float(0x7fc00000);  // NaN: never selected again
-            }
-            __syncwarp();
+        for (int r = lane; r < n_seed; r += 32) {
+            const unsigned long long key = r < m ? best[i * kMaxSeed + r] : kNoKey;
+            out[q * n_seed + r] = key == kNoKey ? -1 : (int32_t)((int64_t)(unsigned)(key & 0xFFFFFFFFull) * n / P);
         }
-        for (int r = m + lane; r < n_seed; r += 32)
-            out[q * n_seed + r] = -1;
     }
 }
 
@@ -185,6 +181,7 @@ using namespace onng;
 extern "C" int onng_seeds_random(uint64_t global_seed, int64_t nq, int64_t n, int32_t n_seed, int32_t *out,
                                  onng_stream_t stream)
 {
+    ONNG_RANGE("onng_seeds_random");
     ONNG_REQUIRE(nq >= 0 && n > 0 && n <= INT32_MAX, ONNG_E_INVAL, "onng_seeds_random: bad sizes");
     ONNG_REQUIRE(n_seed >= 1 && n_seed <= kMaxSeed, ONNG_E_UNSUPPORTED, "onng_seeds_random: n_seed must be in [1, %d]",
                  kMaxSeed);
@@ -206,12 +203,12 @@ extern "C" size_t onng_seeds_pivot_workspace_bytes(int64_t n, int32_t d, int32_t
 extern "C" int onng_seeds_pivot(const float *X, int64_t n, int32_t d, const float *Q, int64_t nq, int32_t n_pivot,
                                 int32_t n_seed, int32_t *out, void *ws, size_t ws_bytes, onng_stream_t stream)
 {
+    ONNG_RANGE("onng_seeds_pivot");
     (void)ws;
     (void)ws_bytes;
     ONNG_REQUIRE(nq >= 0 && n > 0 && n <= INT32_MAX, ONNG_E_INVAL, "onng_seeds_pivot: bad sizes");
     ONNG_REQUIRE(d > 0 && d % 4 == 0, ONNG_E_UNSUPPORTED, "onng_seeds_pivot: d must be a positive multiple of 4");
-    ONNG_REQUIRE(n_pivot >= 1 && n_pivot <= kMaxPivot, ONNG_E_UNSUPPORTED, "onng_seeds_pivot: n_pivot in [1, %d]",
-                 kMaxPivot);
+    ONNG_REQUIRE(n_pivot >= 1, ONNG_E_UNSUPPORTED, "onng_seeds_pivot: n_pivot must be >= 1");
     ONNG_REQUIRE(n_seed >= 1 && n_seed <= kMaxSeed, ONNG_E_UNSUPPORTED, "onng_seeds_pivot: n_seed in [1, %d]",
                  kMaxSeed);
     if (nq == 0)
@@ -219,7 +216,7 @@ extern "C" int onng_seeds_pivot(const float *X, int64_t n, int32_t d, const floa
     ONNG_REQUIRE(X && Q && out, ONNG_E_INVAL, "onng_seeds_pivot: NULL pointer");
     ONNG_REQUIRE(aligned16(X) && aligned16(Q), ONNG_E_INVAL, "onng_seeds_pivot: X and Q must be 16-byte aligned");
     const int P = (int)std::min<int64_t>(n_pivot, n);
-    const size_t sm = pivot_smem_bytes(P);
+    const size_t sm = pivot_smem_bytes();
     ONNG_CUDA_TRY(cudaFuncSetAttribute(reinterpret_cast<const void *>(seeds_pivot_kernel),
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                   "onng_seeds_pivot: smem attribute");

@@ -47,6 +47,7 @@ extern "C" int onng_version(void) { return 1; }
 
 extern "C" int onng_to_bf16(const float *X, int64_t count, uint16_t *out, onng_stream_t stream)
 {
+    ONNG_RANGE("onng_to_bf16");
     ONNG_REQUIRE(count >= 0, ONNG_E_INVAL, "onng_to_bf16: negative count");
     if (count == 0)
         return ONNG_OK;

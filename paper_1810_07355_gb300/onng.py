@@ -20,7 +20,7 @@ _lock = threading.Lock()
 _lib = None
 
 ONNG_OK, ONNG_E_INVAL, ONNG_E_WORKSPACE, ONNG_E_CUDA, ONNG_E_LIMIT, ONNG_E_UNSUPPORTED = range(6)
-FLAG_S_OVERFLOW, FLAG_VISIT_OVERFLOW, FLAG_LIMIT = 1, 2, 4
+FLAG_S_OVERFLOW, FLAG_VISIT_OVERFLOW, FLAG_LIMIT, FLAG_CHECK = 1, 2, 4, 8
 PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 
 
@@ -36,13 +36,21 @@ class _Index(C.Structure):
                 ("X_fp8", C.c_void_p), ("fp8_scale", C.c_void_p)]
 
 
+class _GraphStats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("max_out", C.c_int64), ("max_in", C.c_int64),
+                ("zero_in", C.c_int64), ("mean_out", C.c_double), ("top5_out", C.c_double),
+                ("bottom5_in", C.c_double), ("in_dist10", C.c_double)]
+
+
 class _Params(C.Structure):
     _fields_ = [("k", C.c_int32), ("e_s", C.c_int32), ("eps", C.c_float), ("precision", C.c_int32),
                 ("k_rerank", C.c_int32), ("max_expansions", C.c_int32), ("pool_cap", C.c_int32)]
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this process loads: ``libonng.so``, or the one the
+    ONNG_LIBRARY environment variable names (e.g. the bounds-checked build)."""
+    return os.environ.get("ONNG_LIBRARY") or _build.LIB
 
 
 def load(build_if_missing: bool = True):
@@ -51,11 +59,14 @@ def load(build_if_missing: bool = True):
     with _lock:
         if _lib is not None:
             return _lib
-        if build_if_missing:
+        path = library_path()
+        if build_if_missing and path == _build.LIB:
             _build.build()
-        if not os.path.exists(_build.LIB):
-            raise RuntimeError(f"onng CUDA library not found at {_build.LIB}")
-        lib = C.CDLL(_build.LIB)
+        elif build_if_missing and os.path.abspath(path) == _build.LIB_CHECK:
+            _build.build_checked()
+        if not os.path.exists(path):
+            raise RuntimeError(f"onng CUDA library not found at {path}")
+        lib = C.CDLL(path)
         i32, i64, u64, sz, vp, f32 = C.c_int32, C.c_int64, C.c_uint64, C.c_size_t, C.c_void_p, C.c_float
         sig = {
             "onng_last_error": ([], C.c_char_p),
@@ -92,6 +103,12 @@ def load(build_if_missing: bool = True):
             "onng_mlp_adam": ([vp, vp, vp, vp, i64, f32, f32, f32, f32, vp], C.c_int),
             "onng_mlp_train": ([vp, vp, vp, vp, vp, i64, i32, i64, i64, f32, vp, vp, vp], C.c_int),
             "onng_mlp_predict": ([vp, vp, i64, f32, i32, i32, vp, vp, vp], C.c_int),
+            "onng_graph_stats_workspace_bytes": ([i64, i64], sz),
+            "onng_graph_stats": ([vp, vp, vp, i64, C.POINTER(_GraphStats), vp, sz, vp], C.c_int),
+            "onng_index_save": ([C.c_char_p, vp, vp, vp, vp, i64, i32, vp], C.c_int),
+            "onng_index_check": ([C.c_char_p, vp, vp, vp, vp], C.c_int),
+            "onng_index_load": ([C.c_char_p, i64, i32, i64, vp, vp, vp, vp, vp], C.c_int),
+            "onng_crc32": ([C.c_uint32, vp, sz], C.c_uint32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -112,6 +129,8 @@ def exported_symbols():
         "onng_mlp_loss_grad", "onng_mlp_adam", "onng_mlp_train", "onng_mlp_predict", "onng_search_noalloc", "onng_to_fp8",
         "onng_adjust_degree_sac_workspace_bytes", "onng_adjust_degree_sac_count", "onng_adjust_degree_sac",
         "onng_adjust_path_literal_workspace_bytes", "onng_adjust_path_literal",
+        "onng_graph_stats_workspace_bytes", "onng_graph_stats", "onng_index_save", "onng_index_check",
+        "onng_index_load", "onng_crc32",
     ]
 
 
@@ -246,6 +265,55 @@ def adjust_path_literal(row_ptr: torch.Tensor, col: torch.Tensor, length: torch.
     _check(lib.onng_adjust_path_literal(_ptr(row_ptr), _ptr(col), _ptr(length), n, _ptr(rp), _ptr(oc), _ptr(ol),
                                         C.byref(nnz), _ptr(ws), ws.numel(), _stream()))
     return rp, oc[:nnz.value], ol[:nnz.value]
+
+
+def graph_stats(row_ptr: torch.Tensor, col: torch.Tensor, length: torch.Tensor) -> dict:
+    """Table 4's graph statistics (top-5 % outdegree, bottom-5 % indegree, mean
+    indegree distance over the 10 shortest incoming edges) and the degree extremes."""
+    row_ptr = _dev(row_ptr, torch.int64)
+    col = _dev(col, torch.int32)
+    length = _dev(length, torch.float32)
+    n = row_ptr.numel() - 1
+    lib = load()
+    ws = _ws(lib.onng_graph_stats_workspace_bytes(n, col.numel()), row_ptr.device)
+    out = _GraphStats()
+    _check(lib.onng_graph_stats(_ptr(row_ptr), _ptr(col), _ptr(length), n, C.byref(out), _ptr(ws), ws.numel(),
+                                _stream()))
+    return {name: getattr(out, name) for name, _ in _GraphStats._fields_}
+
+
+# ----------------------------------------------------------------------------- index files
+
+def crc32(data: bytes, crc: int = 0) -> int:
+    """The CRC-32 the index files carry (reflected, polynomial 0xEDB88320)."""
+    buf = C.create_string_buffer(bytes(data), len(data))
+    return int(load().onng_crc32(crc, C.cast(buf, C.c_void_p), len(data)))
+
+
+def index_check(path: str) -> dict:
+    """Header fields of an index file after a full size and CRC check (host only)."""
+    n, d, nnz, has_len = C.c_int64(0), C.c_int32(0), C.c_int64(0), C.c_int32(0)
+    _check(load().onng_index_check(os.fsencode(path), C.byref(n), C.byref(d), C.byref(nnz), C.byref(has_len)))
+    return {"n": n.value, "d": d.value, "nnz": nnz.value, "has_len": bool(has_len.value)}
+
+
+def save_index(index: "Index", path: str):
+    """Writes the graph (with its lengths when the index has them) and the float32
+    vectors; the reduced-precision copies and the padded table are rebuilt on load."""
+    _check(load().onng_index_save(os.fsencode(path), _ptr(index.row_ptr), _ptr(index.col), _ptr(index.length),
+                                  _ptr(index.X), index.n, index.d, _stream()))
+
+
+def load_index(path: str, device="cuda") -> "Index":
+    """Reads an index file written by save_index into new device tensors."""
+    h = index_check(path)
+    rp = torch.empty(h["n"] + 1, dtype=torch.int64, device=device)
+    col = torch.empty(max(h["nnz"], 1), dtype=torch.int32, device=device)
+    ln = torch.empty(max(h["nnz"], 1), dtype=torch.float32, device=device) if h["has_len"] else None
+    X = torch.empty((h["n"], h["d"]), dtype=torch.float32, device=device)
+    _check(load().onng_index_load(os.fsencode(path), h["n"], h["d"], h["nnz"], _ptr(rp), _ptr(col), _ptr(ln),
+                                  _ptr(X), _stream()))
+    return Index(rp, col[:h["nnz"]], X, None, None if ln is None else ln[:h["nnz"]])
 
 
 # ----------------------------------------------------------------------------- seeds

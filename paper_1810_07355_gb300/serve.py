@@ -158,7 +158,7 @@ class ServeResult:
 class Server:
     """Continuous-batching search server over one index on the current device."""
 
-    def __init__(self, index: onng.Index, eps_table: dict, e_s: int, n_pivot: int = 256, n_seed: int = 10,
+    def __init__(self, index: onng.Index, eps_table: dict, e_s: int, n_pivot: int = 1024, n_seed: int = 10,
                  precision: int = onng.PREC_FP32, k_rerank: int = 0, slots: int = 4, ws_budget: int = 1 << 30,
                  max_queries: int = 4096, k_max: int = 100, timeout_s: float = 10.0):
         self.lib = onng.load()
@@ -387,7 +387,7 @@ def serve_spec(seconds: float = 60.0, rate: float = 100_000.0, precisions=("fp8"
     for name in tuple(precisions) + ("fp32",):
         prec = codes[name]
         kr = k_rerank if prec != onng.PREC_FP32 else 0
-        table = calibrate_eps(index, Qcal, ks, recalls, es_opts, 256, 10, prec, kr)
+        table = calibrate_eps(index, Qcal, ks, recalls, es_opts, 1024, 10, prec, kr)
         srv = Server(index, table, e_s, precision=prec, k_rerank=kr, slots=1 if name == "fp32" else slots,
                      ws_budget=budget, timeout_s=timeout_s)
         srv.run(trace[: min(len(trace), 200)], Q)  # warm-up

@@ -89,3 +89,67 @@ def test_reduced_precision_argument_checks(lib):
     assert st == onng.ONNG_E_UNSUPPORTED and b"k_rerank" in lib.onng_last_error()
     assert lib.onng_to_fp8(None, -1, 8, None, None, None) == onng.ONNG_E_INVAL
     assert lib.onng_to_fp8(None, 10, 8, None, None, None) == onng.ONNG_E_INVAL
+
+
+def test_crc32_matches_zlib(lib):
+    import zlib
+    from paper_1810_07355_gb300 import onng
+    rng = os.urandom(4099)
+    for data in (b"", b"123456789", rng):
+        assert onng.crc32(data) == zlib.crc32(data)
+    # continuation: the CRC of a + b from the CRC of a
+    assert onng.crc32(rng[1000:], onng.crc32(rng[:1000])) == zlib.crc32(rng)
+    assert onng.crc32(b"123456789") == 0xCBF43926  # the published check value
+
+
+def _write_index_file(path, row_ptr, col, length, X, version=1, crc=None):
+    """An index file written from the layout the header documents."""
+    import struct
+    import zlib
+    payload = row_ptr.astype("<i8").tobytes() + col.astype("<i4").tobytes()
+    if length is not None:
+        payload += length.astype("<f4").tobytes()
+    payload += X.astype("<f4").tobytes()
+    c = zlib.crc32(payload) if crc is None else crc
+    head = b"ONNGIDX\0" + struct.pack("<IIqiIq", version, 1 if length is not None else 0, len(row_ptr) - 1,
+                                      X.shape[1], c, len(col)) + bytes(24)
+    assert len(head) == 64
+    with open(path, "wb") as f:
+        f.write(head + payload)
+
+
+def test_index_file_check(lib, tmp_path):
+    import numpy as np
+    from paper_1810_07355_gb300 import onng
+    rng = np.random.default_rng(0)
+    rp = np.array([0, 2, 3, 5], np.int64)
+    col = np.array([1, 2, 0, 0, 1], np.int32)
+    ln = rng.random(5).astype(np.float32)
+    X = rng.random((3, 8)).astype(np.float32)
+    good = tmp_path / "g.onng"
+    _write_index_file(good, rp, col, ln, X)
+    assert onng.index_check(str(good)) == {"n": 3, "d": 8, "nnz": 5, "has_len": True}
+    _write_index_file(good, rp, col, None, X)
+    assert onng.index_check(str(good))["has_len"] is False
+    bad = tmp_path / "b.onng"
+    for kw, msg in ((dict(version=2), b"version"), (dict(crc=1), b"CRC")):
+        _write_index_file(bad, rp, col, ln, X, **kw)
+        with pytest.raises(onng.OnngError):
+            onng.index_check(str(bad))
+        assert msg in lib.onng_last_error()
+    # one flipped payload byte, a truncated file, a missing file
+    _write_index_file(bad, rp, col, ln, X)
+    raw = bytearray(bad.read_bytes())
+    raw[100] ^= 1
+    bad.write_bytes(bytes(raw))
+    with pytest.raises(onng.OnngError):
+        onng.index_check(str(bad))
+    bad.write_bytes(bytes(raw[:-4]))
+    with pytest.raises(onng.OnngError):
+        onng.index_check(str(bad))
+    with pytest.raises(onng.OnngError):
+        onng.index_check(str(tmp_path / "missing.onng"))
+    # a load whose sizes disagree with the file is refused before any CUDA call
+    _write_index_file(good, rp, col, ln, X)
+    st = lib.onng_index_load(str(good).encode(), 4, 8, 5, C.c_void_p(8), C.c_void_p(8), None, C.c_void_p(8), None)
+    assert st == onng.ONNG_E_INVAL and b"expects" in lib.onng_last_error()

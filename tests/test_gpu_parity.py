@@ -255,6 +255,16 @@ def test_seeds_pivot_tiles_and_ragged_edges(onng, d, P, nq, n_seed):
     assert np.array_equal(host(s), oracle.seeds_pivot(X, Q, P, n_seed))
 
 
+@pytest.mark.parametrize("d,P,n_seed", [(100, 16384, 10), (128, 5000, 64)])
+def test_seeds_pivot_many_pivots(onng, d, P, n_seed):
+    """More pivots than one query's distances would fit in shared memory: the
+    running best list gives the oracle's ids (ties by pivot index)."""
+    X = synth.small_integers(40000, d, high=6, seed=d + 5)
+    Q = synth.small_integers(70, d, high=6, seed=d + 6)
+    s = onng.seeds_pivot(dev(X), dev(Q), P, n_seed)
+    assert np.array_equal(host(s), oracle.seeds_pivot(X, Q, P, n_seed))
+
+
 # ----------------------------------------------------------------------------- search
 
 @pytest.fixture(scope="module")

@@ -120,7 +120,7 @@ def test_serving_results_equal_alone_and_in_the_mix():
             r = trace[rid]
             q = torch.from_numpy(Q[r["first"]:r["first"] + r["size"]]).cuda()
             k = int(r["k"])
-            s = onng.seeds_pivot(Xd, q, 256, 10)
+            s = onng.seeds_pivot(Xd, q, srv.n_pivot, 10)
             kw = dict(precision=prec, k_rerank=max(20, k)) if prec else {}
             ids, dist, _ = onng.search(index, q, k, 10, eps[(k, float(r["recall"]))], s, **kw)
             assert np.array_equal(ids.cpu().numpy(), res.ids[rid]), rid
@@ -133,7 +133,7 @@ def test_serving_results_equal_alone_and_in_the_mix():
                 r = trace[rid]
                 q = Q[r["first"]:r["first"] + r["size"]]
                 k = int(r["k"])
-                s = onng.seeds_pivot(Xd, torch.from_numpy(q).cuda(), 256, 10).cpu().numpy()
+                s = onng.seeds_pivot(Xd, torch.from_numpy(q).cuda(), srv.n_pivot, 10).cpu().numpy()
                 o = oracle.search(ptr, col, X, q, k, 10, np.float32(eps[(k, float(r["recall"]))]), s, margin=True)
                 st = np.zeros((len(q), 4), np.int64)
                 assert_search_parity(res.ids[rid], res.dist[rid], st, *o, X, q, min_tie_free=0.0, counts=False)
