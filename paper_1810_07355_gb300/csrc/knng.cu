@@ -17,6 +17,11 @@
 //
 // Integer-valued inputs whose squared norms stay below 2^23 are ranked exactly:
 // every product, partial sum and the expanded form are exact in float32.
+//
+// Which sweep runs (onng_knn): byte-valued inputs at d = 64 / 128 take the
+// tensor cores exactly (knn_tc_kernel); other non-integer inputs at d >= 32 take
+// the tensor cores in a split bfloat16 form (knn_tcs_kernel) whose survivors are
+// rescored; everything else, and problems smaller than one tile, the SIMT sweep.
 #include <algorithm>
 #include <cmath>
 
@@ -270,21 +275,33 @@ __global__ void knn_final_kernel(const float *__restrict__ X, int d, const float
 // partial sum is an integer below 2^23, so the float32 accumulation, and with it
 // the ranking, is exact.
 //
-// One CTA owns 128 query rows (the A operand, loaded once by TMA) and sweeps the
-// base in tiles of 256 rows (the B operand, a two-stage TMA ring).  Shared
-// memory holds both operands K-major in 128-byte-swizzled atoms (8 rows x 64
-// bfloat16).  Warp 9 allocates 512 TMEM columns (two 128 x 256 float32
-// accumulators); its lane 0 issues tcgen05.mma (M = 128, N = 256, K = 16 per
-// instruction) and commits to mbarriers that free the smem stage and hand the
-// accumulator to the epilogue.  Warp 8 lane 0 issues the TMA loads.  Warps 0-7
-// read the accumulators with tcgen05.ld (warp w sees TMEM lanes 32 (w % 4) ..
-// +31, i.e. one query row per thread, and columns 128 (w / 4) .. +127), form
-// |q|^2 + |x|^2 - 2 q.x, filter against the row's threshold and append to the
-// row's candidate buffer; rows whose buffer may not absorb another tile are
-// merged between tiles.  Every mbarrier wait gives up after 2 s, records an
-// error code and lets all roles reach the teardown, where TMEM is freed.
-constexpr int TC_M = 128, TC_N = 256, TC_BUF = 384, TC_STAGES = 2;
-constexpr int TC_EPI = 256;                 // epilogue threads (8 warps)
+// One CTA owns 256 query rows, two blocks of 128 (the A operands, loaded once by
+// TMA), and sweeps the base in tiles of 128 rows (the B operand, a three-stage
+// TMA ring) that both row blocks share.  Shared memory holds the operands
+// K-major in 128-byte-swizzled atoms (8 rows x 64 bfloat16).  Warp 9 allocates
+// the 512 TMEM columns: for each row block two 128 x 128 float32 accumulators
+// (tiles alternate between them).  Its lane 0 issues tcgen05.mma (M = 128,
+// N = 128, K = 16 per instruction, both row blocks per K step) and commits to
+// mbarriers that free the smem stage and hand the accumulators to the epilogue.
+// Warp 8 lane 0 issues the TMA loads.
+//
+// Epilogue (warps 0-7): thread (w, l) owns query row 128 (w / 4) + 32 (w % 4) + l
+// outright, reading it from TMEM lanes 32 (w % 4) .. +31 with tcgen05.ld.  Per
+// 32-column chunk it takes the running maximum of q.x - |x|^2 / 2 (the half
+// norms come from a padded global array, the same address for the whole warp);
+// a chunk whose maximum passes the row's threshold appends its hits (|q|^2 +
+// |x|^2 - 2 q.x below the threshold) to the row's candidate buffer.  A row whose
+// buffer may not absorb another tile is merged into its sorted best list by its
+// warp: the buffer is sorted (bitonic, in registers) and a half-cleaner against
+// the reversed best list plus a bitonic merge keep the KC smallest.  No barrier
+// couples the epilogue warps: each arrives on the accumulator's "empty" barrier
+// when its TMEM reads are done and merges afterwards.  Every mbarrier wait gives
+// up after 2 s, records an error code and lets all roles reach the teardown,
+// where TMEM is freed.
+constexpr int TC_M = 128, TC_N = 128, TC_BUF = 256, TC_STAGES = 3;
+constexpr int TC_RB = 2;                    // 128-row blocks per CTA
+constexpr int TC_ROWS = TC_M * TC_RB;       // query rows per CTA
+constexpr int TC_EPI = 256;                 // epilogue threads (8 warps), one per row
 constexpr int TC_THREADS = TC_EPI + 64;     // + TMA warp + MMA warp
 constexpr unsigned long long TC_TIMEOUT_NS = 2000000000ull;
 
@@ -392,7 +409,138 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar)
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+template <int KA> struct TcSmem {
+    static constexpr int A_ATOM = TC_M * 128;   // bytes of one 64-wide K atom of a 128-row block
+    static constexpr int B_ATOM = TC_N * 128;
+    static constexpr int A_BYTES = TC_RB * KA * A_ATOM;
+    static constexpr int B_STAGE = KA * B_ATOM;
+    // alignment slack, operands, then barriers and the TMEM address
+    static constexpr int BYTES = 1024 + A_BYTES + TC_STAGES * B_STAGE + 256;
+};
+
+// Compact warp sorts for the tensor-core epilogue: the stage loops run at run
+// time (only the loop over a lane's registers is unrolled), so the code stays
+// small enough for the instruction cache next to the epilogue's hot loop.
+// Element e = i * 32 + lane lives in v[i] of lane `lane`.
+
+// compare-exchange of registers i and i ^ JR (partners 32 JR elements apart),
+// ascending where bit `size` of the element index is clear
+template <int JR, int N>
+__device__ __forceinline__ void cas_regs(unsigned long long (&v)[N], int lane, int size)
+{
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const int ii = i ^ JR;
+        if (ii > i) {
+            const bool asc = (((i << 5) | lane) & size) == 0;
+            const unsigned long long a = v[i], b = v[ii];
+            const bool sw = asc ? (a > b) : (a < b);
+            v[i] = sw ? b : a;
+            v[ii] = sw ? a : b;
+        }
+    }
+}
+
+// one bitonic step at distance j elements for sequences of length `size`
+template <int N>
+__device__ __forceinline__ void bitonic_step(unsigned long long (&v)[N], int lane, int size, int j)
+{
+    if (j >= 32) {
+        const int jr = j >> 5;
+        if constexpr (N >= 2)
+            if (jr == 1)
+                cas_regs<1>(v, lane, size);
+        if constexpr (N >= 4)
+            if (jr == 2)
+                cas_regs<2>(v, lane, size);
+        if constexpr (N >= 8)
+            if (jr == 4)
+                cas_regs<4>(v, lane, size);
+    } else {
+        const bool lower = (lane & j) == 0;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const bool asc = (((i << 5) | lane) & size) == 0;
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[i], j);
+            const bool take_min = lower == asc;
+            v[i] = take_min ? (o < v[i] ? o : v[i]) : (o > v[i] ? o : v[i]);
+        }
+    }
+}
+
+// ascending sort of 32 N keys
+template <int N> __device__ void warp_sort_compact(unsigned long long (&v)[N], int lane)
+{
+    static_assert(N == 1 || N == 2 || N == 4 || N == 8, "N in {1, 2, 4, 8}");
+#pragma unroll 1
+    for (int size = 2; size <= 32 * N; size <<= 1)
+#pragma unroll 1
+        for (int j = size >> 1; j > 0; j >>= 1)
+            bitonic_step<N>(v, lane, size, j);
+}
+
+// ascending merge of a bitonic sequence of 32 N keys (one bitonic merge pass with
+// every element's direction ascending)
+template <int N> __device__ void warp_merge_compact(unsigned long long (&v)[N], int lane)
+{
+#pragma unroll 1
+    for (int j = 16 * N; j > 0; j >>= 1)
+        bitonic_step<N>(v, lane, 64 * N, j);
+}
+
+// The warp merges row gr's cnt buffered keys into its sorted best list of KC
+// keys and returns the new threshold (the KC-th distance).
+template <int KC>
+__device__ __noinline__ float tc_merge_row(int64_t gr, int cnt, unsigned long long *__restrict__ best,
+                                           const unsigned long long *__restrict__ buf, int lane)
+{
+    static_assert(KC <= TC_BUF && TC_BUF == 256, "the buffer sort holds 256 keys");
+    constexpr int PB = KC / 32;
+    unsigned long long a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int e = i * 32 + lane;
+        a[i] = e < cnt ? buf[gr * TC_BUF + e] : EMPTY_KEY;
+    }
+    warp_sort_compact<8>(a, lane);
+    unsigned long long bv[PB], m[PB];
+#pragma unroll
+    for (int i = 0; i < PB; ++i)
+        bv[i] = best[gr * KC + i * 32 + lane];
+    // half-cleaner of (a[0 .. KC), reversed best): the smaller of each pair is a
+    // bitonic sequence holding the KC smallest keys
+#pragma unroll
+    for (int i = 0; i < PB; ++i) {
+        const unsigned long long br = __shfl_sync(0xffffffffu, bv[PB - 1 - i], 31 - lane);
+        m[i] = a[i] < br ? a[i] : br;
+    }
+    warp_merge_compact<PB>(m, lane);
+#pragma unroll
+    for (int i = 0; i < PB; ++i)
+        best[gr * KC + i * 32 + lane] = m[i];
+    return key_dist(__shfl_sync(0xffffffffu, m[PB - 1], 31));
+}
+
+// a[j] for a run-time j in [0, 32): a five-level select tree (no local memory)
+__device__ __forceinline__ float pick32(const float (&a)[32], int j)
+{
+    float l1[16], l2[8], l3[4];
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        l1[i] = (j & 16) ? a[i + 16] : a[i];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        l2[i] = (j & 8) ? l1[i + 8] : l1[i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        l3[i] = (j & 4) ? l2[i + 4] : l2[i];
+    const float x = (j & 2) ? l3[2] : l3[0], y = (j & 2) ? l3[3] : l3[1];
+    return (j & 1) ? y : x;
+}
+
+// tcgen05.ld of 32 columns without the wait; tmem_wait32 completes it (its
+// operands tie the registers to the wait, so nothing reads them earlier)
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&v)[32])
 {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
                  "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
@@ -403,24 +551,139 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
                    "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
                    "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
                  : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(TC_EPI) : "memory"); }
+__device__ __forceinline__ void tmem_wait32(uint32_t (&v)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                   "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]),
+                   "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]),
+                   "+r"(v[22]), "+r"(v[23]), "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]),
+                   "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
+                 :
+                 : "memory");
+}
 
-template <int KA> struct TcSmem {
-    static constexpr int A_ATOM = TC_M * 128;   // bytes of one 64-wide K atom of A
-    static constexpr int B_ATOM = TC_N * 128;
-    static constexpr int A_BYTES = KA * A_ATOM;
-    static constexpr int B_STAGE = KA * B_ATOM;
-    // alignment slack, operands, then barriers, TMEM address, flags, thresholds,
-    // counts and the base norms of two tiles
-    static constexpr int BYTES = 1024 + A_BYTES + TC_STAGES * B_STAGE + 4096;
-};
+// the half norms of a chunk's 32 columns (loaded right before their use: a load
+// one chunk ahead costs registers the kernel does not have at one CTA per SM)
+__device__ __forceinline__ void load_h(float4 (&h)[8], const float4 *__restrict__ p)
+{
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        h[i] = __ldg(p + i);
+}
+
+// One 32-column chunk of a row: the running maximum of q.x - |x|^2 / 2 decides
+// whether any column passes; a passing lane builds its hit mask and appends each
+// hit's (distance, id) key to the row's buffer.
+__device__ __forceinline__ void tc_chunk(const uint32_t (&v)[32], const float4 (&hq)[8], float tr, float qnr,
+                                         int64_t cb, int64_t self, unsigned long long *__restrict__ brow, int &cnt)
+{
+    float a[32];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float4 x = hq[i];
+        a[4 * i] = __uint_as_float(v[4 * i]) - x.x;
+        a[4 * i + 1] = __uint_as_float(v[4 * i + 1]) - x.y;
+        a[4 * i + 2] = __uint_as_float(v[4 * i + 2]) - x.z;
+        a[4 * i + 3] = __uint_as_float(v[4 * i + 3]) - x.w;
+    }
+    float m0 = a[0], m1 = a[1], m2 = a[2], m3 = a[3];
+#pragma unroll
+    for (int j = 4; j < 32; j += 4) {
+        m0 = fmaxf(m0, a[j]);
+        m1 = fmaxf(m1, a[j + 1]);
+        m2 = fmaxf(m2, a[j + 2]);
+        m3 = fmaxf(m3, a[j + 3]);
+    }
+    if (!(fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) > tr))
+        return;
+    unsigned hit = 0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+        hit |= (a[j] > tr ? 1u : 0u) << j;
+    const int64_t sj = self - cb;
+    if (sj >= 0 && sj < 32)
+        hit &= ~(1u << (int)sj);
+    while (hit) {
+        const int j = __ffs(hit) - 1;
+        hit &= hit - 1;
+        brow[cnt++] = pack_key(fmaxf(qnr - 2.f * pick32(a, j), 0.f), (int)(cb + j));
+    }
+}
+
+// The epilogue of the tensor-core kernels (warps 0-7; see knn_tc_kernel): one
+// query row per thread, tile by tile from the TMEM accumulators (row block rb =
+// warp / 4 at columns (2 rb + b) * TC_N, b = tile & 1).
+template <int KC>
+__device__ void tc_epilogue(uint64_t *accf, uint64_t *acce, uint32_t tmem, int warp, int lane, int64_t row0,
+                            int64_t nq, int64_t tiles, int64_t self_offset, const float *__restrict__ xh,
+                            const float *__restrict__ qn, unsigned long long *__restrict__ best,
+                            unsigned long long *__restrict__ buf, int *err)
+{
+    const int rb = warp >> 2, qd = warp & 3;
+    const int64_t grow = row0 + rb * TC_M + qd * 32 + lane;
+    const bool row_ok = grow < nq;
+    const float qnr = row_ok ? qn[grow] : 0.f;
+    const int64_t self = (self_offset >= 0 && row_ok) ? self_offset + grow : -1;
+    float thr = row_ok ? INFINITY : -INFINITY;
+    int cnt = 0;
+    unsigned long long *brow = buf + (row_ok ? grow : 0) * TC_BUF;
+    const uint32_t lane_base = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(rb * 2 * TC_N);
+    for (int64_t t = 0; t < tiles; ++t) {
+        const int b = (int)(t & 1);
+        const bool ok = mbar_wait(&accf[b], (uint32_t)((t >> 1) & 1), err, 5);
+        if (!__all_sync(0xffffffffu, ok))
+            break;
+        tc_fence_after();
+        const int64_t col0 = t * TC_N;
+        // d^2 = |q|^2 + |x|^2 - 2 q.x < thr  <=>  q.x - |x|^2 / 2 > (|q|^2 - thr) / 2, every
+        // term an exact integer or half-integer for byte-valued inputs (approximate in
+        // the split float form, whose survivors are rescored)
+        const float tr = 0.5f * (qnr - thr);
+        const float4 *h4 = reinterpret_cast<const float4 *>(xh + col0);
+        const uint32_t tb = lane_base + (uint32_t)(b * TC_N);
+        // TMEM loads run one chunk ahead of the filter (chunk pairs: va even, vb odd)
+        uint32_t va[32], vb[32];
+        float4 hq[8];
+        tmem_ld32_async(tb, va);
+        tmem_wait32(va);
+#pragma unroll 1
+        for (int c = 0; c < TC_N / 32; c += 2) {
+            tmem_ld32_async(tb + (uint32_t)((c + 1) * 32), vb);
+            load_h(hq, h4 + c * 8);
+            tc_chunk(va, hq, tr, qnr, col0 + c * 32, self, brow, cnt);
+            tmem_wait32(vb);
+            if (c + 2 < TC_N / 32)
+                tmem_ld32_async(tb + (uint32_t)((c + 2) * 32), va);
+            load_h(hq, h4 + (c + 1) * 8);
+            tc_chunk(vb, hq, tr, qnr, col0 + (c + 1) * 32, self, brow, cnt);
+            if (c + 2 < TC_N / 32)
+                tmem_wait32(va);
+        }
+        tc_fence_before();
+        mbar_arrive(&acce[b]);
+        // rows whose buffer may not absorb another tile (or all, after the last)
+        const bool last = t + 1 == tiles;
+        unsigned need = __ballot_sync(0xffffffffu, row_ok && (cnt > TC_BUF - TC_N || (last && cnt > 0)));
+        while (need) {
+            const int src = __ffs(need) - 1;
+            need &= need - 1;
+            const int64_t gr = __shfl_sync(0xffffffffu, grow, src);
+            const int c = __shfl_sync(0xffffffffu, cnt, src);
+            const float nt = tc_merge_row<KC>(gr, c, best, buf, lane);
+            if (lane == src) {
+                thr = nt;
+                cnt = 0;
+            }
+        }
+    }
+}
 
 template <int KC, int KA>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n,
-                  int64_t nq, int64_t self_offset, const float *__restrict__ xn, const float *__restrict__ qn,
+                  int64_t nq, int64_t self_offset, const float *__restrict__ xh, const float *__restrict__ qn,
                   unsigned long long *__restrict__ best, unsigned long long *__restrict__ buf, int *err)
 {
     using L = TcSmem<KA>;
@@ -431,14 +694,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint64_t *bars = reinterpret_cast<uint64_t *>(sB + TC_STAGES * L::B_STAGE);
     uint64_t *full = bars, *empty = bars + TC_STAGES, *accf = bars + 2 * TC_STAGES, *acce = accf + 2, *abar = acce + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(abar + 1);
-    int *s_ok = reinterpret_cast<int *>(tmem_slot + 1);
-    float *s_thr = reinterpret_cast<float *>(s_ok + 4);
-    int *s_cnt = reinterpret_cast<int *>(s_thr + TC_M);
-    float *s_xn = reinterpret_cast<float *>(s_cnt + TC_M);  // [2][TC_N], +inf past n
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t row0 = (int64_t)blockIdx.x * TC_M;
+    const int64_t row0 = (int64_t)blockIdx.x * TC_ROWS;
     const int64_t tiles = (n + TC_N - 1) / TC_N;
+    const int nrb = row0 + TC_M < nq ? TC_RB : 1;  // row blocks holding any query row
 
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
@@ -457,11 +717,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    for (int r = tid; r < TC_M; r += blockDim.x) {
-        s_thr[r] = INFINITY;
-        s_cnt[r] = 0;
-    }
-    for (int e = tid; e < TC_M * KC; e += blockDim.x) {
+    for (int e = tid; e < TC_ROWS * KC; e += blockDim.x) {
         const int64_t gr = row0 + e / KC;
         if (gr < nq)
             best[gr * KC + e % KC] = EMPTY_KEY;
@@ -475,9 +731,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
             int64_t issued = 0;
-            mbar_expect_tx(abar, L::A_BYTES);
-            for (int a = 0; a < KA; ++a)
-                tma_load_2d(sA + a * L::A_ATOM, &tmA, a * 64, (int)row0, abar);
+            mbar_expect_tx(abar, nrb * KA * L::A_ATOM);
+            for (int rb = 0; rb < nrb; ++rb)
+                for (int a = 0; a < KA; ++a)
+                    tma_load_2d(sA + (rb * KA + a) * L::A_ATOM, &tmA, a * 64, (int)(row0 + rb * TC_M), abar);
             for (int64_t t = 0; t < tiles; ++t) {
                 const int s = (int)(t % TC_STAGES);
                 if (t >= TC_STAGES && !mbar_wait(&empty[s], (uint32_t)(((t / TC_STAGES) & 1) ^ 1), err, 1))
@@ -505,13 +762,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (t >= 2 && !mbar_wait(&acce[b], (uint32_t)(((t >> 1) & 1) ^ 1), err, 4))
                     break;
                 tc_fence_after();
-                const uint32_t aa = smem_u32(sA), bb = smem_u32(sB + s * L::B_STAGE);
+                const uint32_t bb = smem_u32(sB + s * L::B_STAGE);
 #pragma unroll
-                for (int kk = 0; kk < 4 * KA; ++kk) {
-                    const uint32_t off = (uint32_t)((kk & 3) * 32);  // 16 bf16 = 32 bytes inside the atom
-                    const uint64_t ad = umma_desc(aa + (kk >> 2) * L::A_ATOM + off);
-                    const uint64_t bd = umma_desc(bb + (kk >> 2) * L::B_ATOM + off);
-                    umma_bf16(tmem + (uint32_t)(b * TC_N), ad, bd, idesc, kk > 0 ? 1u : 0u);
+                for (int rb = 0; rb < TC_RB; ++rb) {
+                    if (rb >= nrb)
+                        break;
+                    const uint32_t aa = smem_u32(sA + rb * KA * L::A_ATOM);
+#pragma unroll
+                    for (int kk = 0; kk < 4 * KA; ++kk) {
+                        const uint32_t off = (uint32_t)((kk & 3) * 32);  // 16 bf16 = 32 bytes inside the atom
+                        const uint64_t ad = umma_desc(aa + (kk >> 2) * L::A_ATOM + off);
+                        const uint64_t bd = umma_desc(bb + (kk >> 2) * L::B_ATOM + off);
+                        umma_bf16(tmem + (uint32_t)((rb * 2 + b) * TC_N), ad, bd, idesc, kk > 0 ? 1u : 0u);
+                    }
                 }
                 umma_commit(&empty[s]);
                 umma_commit(&accf[b]);
@@ -523,90 +786,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else {
         // ------------------------------------------------ epilogue (warps 0-7)
-        // Thread (warp w, lane l) owns query row r = 32 (w % 4) + l and columns
-        // 128 (w / 4) .. +127 of each tile.  The tile's base norms are staged in
-        // shared memory one tile ahead (+inf past n, so no bounds test is needed);
-        // the self column is cleared from a chunk's hit mask, and only hits leave
-        // the fast path.
-        const int qd = warp & 3, half = warp >> 2;
-        const int r = qd * 32 + lane;
-        const int64_t grow = row0 + r;
-        const bool row_ok = grow < nq;
-        const float qnr = row_ok ? qn[grow] : 0.f;
-        const int64_t self = (self_offset >= 0 && row_ok) ? self_offset + grow : -1;
-        float thr = row_ok ? INFINITY : -INFINITY;
-        s_xn[tid] = tid < n ? 0.5f * xn[tid] : INFINITY;
-        // the half norm this thread stages for the next tile, loaded one tile ahead
-        // so that its latency never sits in front of a barrier
-        float xn_next = TC_N + tid < n ? 0.5f * xn[TC_N + tid] : INFINITY;
-        epi_sync();
-        for (int64_t t = 0; t < tiles; ++t) {
-            const int b = (int)(t & 1);
-            if (tid == 0)
-                s_ok[0] = mbar_wait(&accf[b], (uint32_t)((t >> 1) & 1), err, 5) ? 1 : 0;
-            epi_sync();
-            if (!s_ok[0])
-                break;
-            tc_fence_after();
-            const int64_t col0 = t * TC_N + half * 128;
-            const float *hs = s_xn + b * TC_N + half * 128;  // |x|^2 / 2 of the tile's columns
-            const int64_t self_local = self - col0;  // in [0, 128) when the self column is here
-            // d^2 = |q|^2 + |x|^2 - 2 q.x < thr  <=>  q.x - |x|^2 / 2 > (|q|^2 - thr) / 2, every term
-            // an exact integer or half-integer here; the running maximum of the left side
-            // decides a chunk, and only a chunk with a hit forms distances
-            const float tr = 0.5f * (qnr - thr);
-#pragma unroll 1
-            for (int c = 0; c < 4; ++c) {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * TC_N + half * 128 + c * 32), v);
-                float mx = -INFINITY;
-#pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    mx = fmaxf(mx, __uint_as_float(v[j]) - hs[c * 32 + j]);
-                if (!(mx > tr))
-                    continue;
-                uint32_t hit = 0;
-#pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    hit |= (__uint_as_float(v[j]) - hs[c * 32 + j] > tr ? 1u : 0u) << j;
-                const int64_t sj = self_local - c * 32;
-                if (sj >= 0 && sj < 32)
-                    hit &= ~(1u << (int)sj);
-                while (hit) {
-                    const int j = __ffs(hit) - 1;
-                    hit &= hit - 1;
-                    float aj = __uint_as_float(v[0]) - hs[c * 32];
-#pragma unroll
-                    for (int u = 1; u < 32; ++u)
-                        aj = u == j ? __uint_as_float(v[u]) - hs[c * 32 + u] : aj;
-                    const float dj = fmaxf(qnr - 2.f * aj, 0.f);
-                    const int pos = atomicAdd(&s_cnt[r], 1);
-                    buf[grow * TC_BUF + pos] = pack_key(dj, (int)(col0 + c * 32 + j));
-                }
-            }
-            tc_fence_before();
-            mbar_arrive(&acce[b]);
-            // stage the next tile's half norms into the other half of s_xn, and load
-            // those of the tile after it
-            s_xn[(b ^ 1) * TC_N + tid] = xn_next;
-            {
-                const int64_t nc = (t + 2) * TC_N + tid;
-                xn_next = nc < n ? 0.5f * xn[nc] : INFINITY;
-            }
-            epi_sync();
-            const bool last = t + 1 == tiles;
-            for (int rr = warp; rr < TC_M; rr += TC_EPI / 32) {
-                const int64_t gr = row0 + rr;
-                if (gr >= nq)
-                    break;
-                const int cnt = s_cnt[rr];
-                if (cnt > TC_BUF - TC_N || (last && cnt > 0))
-                    merge_row<KC, TC_BUF>(rr, gr, best, buf, s_thr, s_cnt, lane);
-            }
-            epi_sync();
-            if (row_ok)
-                thr = s_thr[r];
-        }
+        tc_epilogue<KC>(accf, acce, tmem, warp, lane, row0, nq, tiles, self_offset, xh, qn, best, buf, err);
     }
     tc_fence_before();
     __syncthreads();
@@ -616,18 +796,229 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
-// Sets *flag if any of the values is not an integer in [0, 255] (byte-valued
-// descriptors: exact in bfloat16, and at d <= 128 every squared norm, dot product,
-// |x|^2 / 2 and distance of the tensor-core path is an exact float32 below 2^23).
-__global__ void bf16_exact_kernel(const float *__restrict__ x, int64_t count, int *flag)
+// ---------------------------------------------------------------- float inputs
+//
+// knn_tcs_kernel: the tensor-core sweep for float inputs.  Both vector sets are
+// first centred on the mean of the base (distances do not change) and split into
+// bfloat16 pairs c = hi + lo with hi = bf16(c), lo = bf16(c - hi); a dot product
+// is then qh.xh + qh.xl + ql.xh in float32 (three tcgen05.mma per K step; the
+// dropped ql.xl and the rounding of lo are below 2^-16 |q| |x|).  The ranking of
+// this expanded form only selects the KC survivors of a row, which
+// knn_final_kernel rescores by direct difference in float32 from the original
+// vectors, as for the SIMT sweep.  Rows are zero-padded to dp = 64 ceil(d / 64),
+// so K runs in chunks of one 64-wide atom: A (both row blocks, hi and lo) and B
+// (hi and lo) stream through a two-stage ring of 96 KB, the accumulators stay in
+// TMEM across the chunks of a tile, and the epilogue is tc_epilogue.
+constexpr int TCS_STAGES = 2;
+struct TcsSmem {
+    static constexpr int ATOM = TC_M * 128;  // 128 rows x 64 bfloat16 (TC_N == TC_M)
+    static constexpr int STAGE = 6 * ATOM;   // A hi (2 blocks), A lo (2 blocks), B hi, B lo
+    static constexpr int BYTES = 1024 + TCS_STAGES * STAGE + 256;
+};
+static_assert(TC_N == TC_M, "the split kernel's atoms are 128 rows for A and B alike");
+
+template <int KC>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    knn_tcs_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                   const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int64_t n,
+                   int64_t nq, int nk, int64_t self_offset, const float *__restrict__ xh,
+                   const float *__restrict__ qn, unsigned long long *__restrict__ best,
+                   unsigned long long *__restrict__ buf, int *err)
 {
-    int bad = 0;
+    using L = TcsSmem;
+    extern __shared__ unsigned char tc_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + TCS_STAGES * L::STAGE);
+    uint64_t *full = bars, *empty = bars + TCS_STAGES, *accf = bars + 2 * TCS_STAGES, *acce = accf + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acce + 2);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t row0 = (int64_t)blockIdx.x * TC_ROWS;
+    const int64_t tiles = (n + TC_N - 1) / TC_N;
+    const int64_t steps = tiles * nk;
+    const int nrb = row0 + TC_M < nq ? TC_RB : 1;  // row blocks holding any query row
+
+    if (tid == 0) {
+        for (int s = 0; s < TCS_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], TC_EPI);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 9) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int e = tid; e < TC_ROWS * KC; e += blockDim.x) {
+        const int64_t gr = row0 + e / KC;
+        if (gr < nq)
+            best[gr * KC + e % KC] = EMPTY_KEY;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 8) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            const uint32_t bytes = (uint32_t)((2 * nrb + 2) * L::ATOM);
+            int64_t issued = 0;
+            for (int64_t step = 0; step < steps; ++step) {
+                const int s = (int)(step % TCS_STAGES);
+                const int64_t t = step / nk;
+                const int kc = (int)(step % nk);
+                if (step >= TCS_STAGES &&
+                    !mbar_wait(&empty[s], (uint32_t)(((step / TCS_STAGES) & 1) ^ 1), err, 1))
+                    break;
+                unsigned char *st = base + s * L::STAGE;
+                mbar_expect_tx(&full[s], bytes);
+                for (int rb = 0; rb < nrb; ++rb) {
+                    tma_load_2d(st + rb * L::ATOM, &tmAh, kc * 64, (int)(row0 + rb * TC_M), &full[s]);
+                    tma_load_2d(st + (2 + rb) * L::ATOM, &tmAl, kc * 64, (int)(row0 + rb * TC_M), &full[s]);
+                }
+                tma_load_2d(st + 4 * L::ATOM, &tmBh, kc * 64, (int)(t * TC_N), &full[s]);
+                tma_load_2d(st + 5 * L::ATOM, &tmBl, kc * 64, (int)(t * TC_N), &full[s]);
+                issued = step + 1;
+            }
+            // our copies in flight complete before the CTA may exit (bounded)
+            for (int64_t step = issued > TCS_STAGES ? issued - TCS_STAGES : 0; step < issued; ++step)
+                mbar_drain(&full[step % TCS_STAGES], (uint32_t)((step / TCS_STAGES) & 1), err, 6);
+        }
+    } else if (warp == 9) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = umma_idesc(TC_M, TC_N);
+            int64_t last = -1;  // the last step whose MMAs were issued (and committed to empty)
+            for (int64_t step = 0; step < steps; ++step) {
+                const int s = (int)(step % TCS_STAGES);
+                const int64_t t = step / nk;
+                const int kc = (int)(step % nk), b = (int)(t & 1);
+                if (!mbar_wait(&full[s], (uint32_t)((step / TCS_STAGES) & 1), err, 3))
+                    break;
+                if (kc == 0 && t >= 2 && !mbar_wait(&acce[b], (uint32_t)(((t >> 1) & 1) ^ 1), err, 4))
+                    break;
+                tc_fence_after();
+                const uint32_t st = smem_u32(base + s * L::STAGE);
+#pragma unroll
+                for (int rb = 0; rb < TC_RB; ++rb) {
+                    if (rb >= nrb)
+                        break;
+                    const uint32_t dt = tmem + (uint32_t)((rb * 2 + b) * TC_N);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint32_t off = (uint32_t)(kk * 32);  // 16 bf16 = 32 bytes inside the atom
+                        const uint64_t ah = umma_desc(st + rb * L::ATOM + off);
+                        const uint64_t al = umma_desc(st + (2 + rb) * L::ATOM + off);
+                        const uint64_t bh = umma_desc(st + 4 * L::ATOM + off);
+                        const uint64_t bl = umma_desc(st + 5 * L::ATOM + off);
+                        umma_bf16(dt, ah, bh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                        umma_bf16(dt, ah, bl, idesc, 1u);
+                        umma_bf16(dt, al, bh, idesc, 1u);
+                    }
+                }
+                umma_commit(&empty[s]);
+                if (kc == nk - 1)
+                    umma_commit(&accf[b]);
+                last = step;
+            }
+            // the MMAs issued so far complete before TMEM is freed (bounded)
+            if (last >= 0)
+                mbar_drain(&empty[last % TCS_STAGES], (uint32_t)((last / TCS_STAGES) & 1), err, 7);
+        }
+    } else {
+        // ------------------------------------------------ epilogue (warps 0-7)
+        tc_epilogue<KC>(accf, acce, tmem, warp, lane, row0, nq, tiles, self_offset, xh, qn, best, buf, err);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 9) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    }
+}
+
+// sums[j] += the base's coordinates j (float64), for the centring mean
+__global__ void col_sums_kernel(const float *__restrict__ X, int64_t n, int d, double *__restrict__ sums)
+{
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = (int64_t)blockIdx.x * per, r1 = r0 + per < n ? r0 + per : n;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        double acc = 0.0;
+        for (int64_t r = r0; r < r1; ++r)
+            acc += (double)X[r * d + j];
+        if (r1 > r0)
+            atomicAdd(&sums[j], acc);
+    }
+}
+
+__global__ void mean_kernel(const double *__restrict__ sums, int64_t n, int d, float *__restrict__ mu)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d; j += gridDim.x * blockDim.x)
+        mu[j] = (float)(sums[j] / (double)n);
+}
+
+// Row r of M [rows, d] centred on mu, split into bfloat16 hi / lo rows of
+// length dp (zeros past d), and its centred squared norm (half of it when
+// `half`; +inf for the padded rows rows .. padded_rows of a half-norm array).
+__global__ void split_rows_kernel(const float *__restrict__ M, int64_t rows, int d, int dp,
+                                  const float *__restrict__ mu, __nv_bfloat16 *__restrict__ hi,
+                                  __nv_bfloat16 *__restrict__ lo, float *__restrict__ norm, bool half,
+                                  int64_t padded_rows)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < padded_rows;
+         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        if (r >= rows) {
+            if (lane == 0)
+                norm[r] = INFINITY;
+            continue;
+        }
+        float s = 0.f;
+        for (int j = lane; j < dp; j += 32) {
+            const float c = j < d ? M[r * d + j] - mu[j] : 0.f;
+            const __nv_bfloat16 h = __float2bfloat16_rn(c);
+            hi[r * dp + j] = h;
+            lo[r * dp + j] = __float2bfloat16_rn(c - __bfloat162float(h));
+            s = fmaf(c, c, s);
+        }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1)
+            s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0)
+            norm[r] = half ? 0.5f * s : s;
+    }
+}
+
+// xh[i] = |x_i|^2 / 2 for i < n, +inf up to the padded length (no column past n
+// can pass the threshold test).
+__global__ void half_norms_kernel(const float *__restrict__ xn, int64_t n, int64_t padded, float *__restrict__ xh)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < padded; i += (int64_t)gridDim.x * blockDim.x)
+        xh[i] = i < n ? 0.5f * xn[i] : INFINITY;
+}
+
+// Sets bit 0 of *flag if any value is not an integer in [0, 255] (byte-valued
+// descriptors: exact in bfloat16, and at d <= 128 every squared norm, dot product,
+// |x|^2 / 2 and distance of the tensor-core path is an exact float32 below 2^23),
+// and bit 1 if any value is not an integer at all.
+__global__ void value_kind_kernel(const float *__restrict__ x, int64_t count, int *flag)
+{
+    unsigned bad = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
         const float v = x[i];
-        bad |= !(v == rintf(v) && v >= 0.f && v <= 255.f);
+        const bool integer = v == rintf(v);
+        bad |= (integer && v >= 0.f && v <= 255.f) ? 0u : 1u;
+        bad |= integer ? 0u : 2u;
     }
-    if (__syncthreads_or(bad) && threadIdx.x == 0)
-        atomicOr(flag, 1);
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && bad)
+        atomicOr(flag, (int)bad);
 }
 
 __global__ void f32_to_bf16_kernel(const float *__restrict__ x, int64_t count, __nv_bfloat16 *__restrict__ y)
@@ -691,25 +1082,26 @@ int launch(const float *X, int64_t n, int d, const float *Q, int64_t nq, int k, 
 
 template <int KC, int KA>
 int launch_tc_kc(const CUtensorMap &ma, const CUtensorMap &mb, int64_t n, int64_t nq, int64_t self_offset,
-                 const float *xn, const float *qn, unsigned long long *best, unsigned long long *bufp, int *err,
+                 const float *xh, const float *qn, unsigned long long *best, unsigned long long *bufp, int *err,
                  cudaStream_t s)
 {
     const size_t smem = TcSmem<KA>::BYTES;
     ONNG_CUDA_TRY(cudaFuncSetAttribute(reinterpret_cast<const void *>(knn_tc_kernel<KC, KA>),
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                   "onng_knn: tensor kernel smem attribute");
-    knn_tc_kernel<KC, KA><<<(unsigned)((nq + TC_M - 1) / TC_M), TC_THREADS, smem, s>>>(ma, mb, n, nq, self_offset, xn,
-                                                                                     qn, best, bufp, err);
+    knn_tc_kernel<KC, KA><<<(unsigned)((nq + TC_ROWS - 1) / TC_ROWS), TC_THREADS, smem, s>>>(
+        ma, mb, n, nq, self_offset, xh, qn, best, bufp, err);
     return check_launch("onng_knn: tensor kernel");
 }
 
 int launch_tc(const float *X, int64_t n, int d, const float *Q, int64_t nq, int k, int kc, int64_t self_offset,
-              int32_t *nbr, float *len, float *xn, float *qn, unsigned long long *best, unsigned long long *bufp,
-              int *err, __nv_bfloat16 *xb, __nv_bfloat16 *qb, cudaStream_t s)
+              int32_t *nbr, float *len, const float *xn, float *xh, float *qn, unsigned long long *best,
+              unsigned long long *bufp, int *err, __nv_bfloat16 *xb, __nv_bfloat16 *qb, cudaStream_t s)
 {
     const int gb = num_sms() * 8;
     f32_to_bf16_kernel<<<gb, 256, 0, s>>>(X, n * d, xb);
     f32_to_bf16_kernel<<<gb, 256, 0, s>>>(Q, nq * d, qb);
+    half_norms_kernel<<<gb, 256, 0, s>>>(xn, n, (n + TC_N - 1) / TC_N * TC_N, xh);
     int st = check_launch("onng_knn: bf16 copies");
     if (st)
         return st;
@@ -718,14 +1110,14 @@ int launch_tc(const float *X, int64_t n, int d, const float *Q, int64_t nq, int 
         return st;
     const int ka = d / 64;
     if (kc == 32)
-        st = ka == 1 ? launch_tc_kc<32, 1>(ma, mb, n, nq, self_offset, xn, qn, best, bufp, err, s)
-                     : launch_tc_kc<32, 2>(ma, mb, n, nq, self_offset, xn, qn, best, bufp, err, s);
+        st = ka == 1 ? launch_tc_kc<32, 1>(ma, mb, n, nq, self_offset, xh, qn, best, bufp, err, s)
+                     : launch_tc_kc<32, 2>(ma, mb, n, nq, self_offset, xh, qn, best, bufp, err, s);
     else if (kc == 64)
-        st = ka == 1 ? launch_tc_kc<64, 1>(ma, mb, n, nq, self_offset, xn, qn, best, bufp, err, s)
-                     : launch_tc_kc<64, 2>(ma, mb, n, nq, self_offset, xn, qn, best, bufp, err, s);
+        st = ka == 1 ? launch_tc_kc<64, 1>(ma, mb, n, nq, self_offset, xh, qn, best, bufp, err, s)
+                     : launch_tc_kc<64, 2>(ma, mb, n, nq, self_offset, xh, qn, best, bufp, err, s);
     else
-        st = ka == 1 ? launch_tc_kc<128, 1>(ma, mb, n, nq, self_offset, xn, qn, best, bufp, err, s)
-                     : launch_tc_kc<128, 2>(ma, mb, n, nq, self_offset, xn, qn, best, bufp, err, s);
+        st = ka == 1 ? launch_tc_kc<128, 1>(ma, mb, n, nq, self_offset, xh, qn, best, bufp, err, s)
+                     : launch_tc_kc<128, 2>(ma, mb, n, nq, self_offset, xh, qn, best, bufp, err, s);
     if (st)
         return st;
     int code = 0;
@@ -746,6 +1138,62 @@ int launch_tc(const float *X, int64_t n, int d, const float *Q, int64_t nq, int 
     return check_launch("onng_knn: final kernel");
 }
 
+template <int KC>
+int launch_tcs_kc(const CUtensorMap *m, int64_t n, int64_t nq, int nk, int64_t self_offset, const float *xh,
+                  const float *qn, unsigned long long *best, unsigned long long *bufp, int *err, cudaStream_t s)
+{
+    const size_t smem = TcsSmem::BYTES;
+    ONNG_CUDA_TRY(cudaFuncSetAttribute(reinterpret_cast<const void *>(knn_tcs_kernel<KC>),
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                  "onng_knn: split tensor kernel smem attribute");
+    knn_tcs_kernel<KC><<<(unsigned)((nq + TC_ROWS - 1) / TC_ROWS), TC_THREADS, smem, s>>>(
+        m[0], m[1], m[2], m[3], n, nq, nk, self_offset, xh, qn, best, bufp, err);
+    return check_launch("onng_knn: split tensor kernel");
+}
+
+// Float inputs on the tensor cores: centre, split into bfloat16 hi / lo, sweep
+// (knn_tcs_kernel), rescore the survivors from the original vectors.
+int launch_tcs(const float *X, int64_t n, int d, const float *Q, int64_t nq, int k, int kc, int64_t self_offset,
+               int32_t *nbr, float *len, float *xh, float *qn, unsigned long long *best, unsigned long long *bufp,
+               int *err, __nv_bfloat16 *xs, __nv_bfloat16 *qs, double *sums, float *mu, cudaStream_t s)
+{
+    const int dp = (d + 63) / 64 * 64;
+    const int gb = num_sms() * 8;
+    __nv_bfloat16 *xhi = xs, *xlo = xs + (size_t)n * dp;
+    __nv_bfloat16 *qhi = qs, *qlo = qs + (size_t)nq * dp;
+    ONNG_CUDA_TRY(cudaMemsetAsync(sums, 0, sizeof(double) * (size_t)d, s), "onng_knn: clear sums");
+    col_sums_kernel<<<(unsigned)std::min<int64_t>(n, 1024), 256, 0, s>>>(X, n, d, sums);
+    mean_kernel<<<(d + 255) / 256, 256, 0, s>>>(sums, n, d, mu);
+    split_rows_kernel<<<gb, 256, 0, s>>>(X, n, d, dp, mu, xhi, xlo, xh, true, (n + TC_N - 1) / TC_N * TC_N);
+    split_rows_kernel<<<gb, 256, 0, s>>>(Q, nq, d, dp, mu, qhi, qlo, qn, false, nq);
+    int st = check_launch("onng_knn: split copies");
+    if (st)
+        return st;
+    CUtensorMap m[4];
+    if ((st = make_map(&m[0], qhi, nq, dp, TC_M)) || (st = make_map(&m[1], qlo, nq, dp, TC_M)) ||
+        (st = make_map(&m[2], xhi, n, dp, TC_N)) || (st = make_map(&m[3], xlo, n, dp, TC_N)))
+        return st;
+    const int nk = dp / 64;
+    st = kc == 32 ? launch_tcs_kc<32>(m, n, nq, nk, self_offset, xh, qn, best, bufp, err, s)
+         : kc == 64 ? launch_tcs_kc<64>(m, n, nq, nk, self_offset, xh, qn, best, bufp, err, s)
+                    : launch_tcs_kc<128>(m, n, nq, nk, self_offset, xh, qn, best, bufp, err, s);
+    if (st)
+        return st;
+    int code = 0;
+    ONNG_CUDA_TRY(cudaMemcpyAsync(&code, err, sizeof(int), cudaMemcpyDeviceToHost, s), "onng_knn: error flag");
+    ONNG_CUDA_TRY(cudaStreamSynchronize(s), "onng_knn: split tensor kernel");
+    if (code)
+        return set_error(ONNG_E_LIMIT, "onng_knn: tensor-core pipeline wait timed out (role %d)", code);
+    const unsigned grid = (unsigned)((nq * 32 + 255) / 256);
+    if (kc == 32)
+        knn_final_kernel<32><<<grid, 256, 0, s>>>(X, d, Q, nq, best, k, nbr, len);
+    else if (kc == 64)
+        knn_final_kernel<64><<<grid, 256, 0, s>>>(X, d, Q, nq, best, k, nbr, len);
+    else
+        knn_final_kernel<128><<<grid, 256, 0, s>>>(X, d, Q, nq, best, k, nbr, len);
+    return check_launch("onng_knn: final kernel");
+}
+
 }  // namespace
 }  // namespace onng
 
@@ -760,8 +1208,13 @@ extern "C" size_t onng_knn_workspace_bytes(int64_t n, int32_t d, int64_t nq, int
     c.take<unsigned long long>((size_t)std::max<int64_t>(nq, 1) * (kc ? kc : 32));
     c.take<unsigned long long>((size_t)std::max<int64_t>(nq, 1) * std::max(BUF, TC_BUF));
     c.take<int>(64);
-    c.take<__nv_bfloat16>((size_t)std::max<int64_t>(n, 1) * std::max(d, 1));
-    c.take<__nv_bfloat16>((size_t)std::max<int64_t>(nq, 1) * std::max(d, 1));
+    // bfloat16 copies: hi and lo rows of dp = 64 ceil(d / 64) (the byte path uses the hi half)
+    const size_t dp = (size_t)(std::max(d, 1) + 63) / 64 * 64;
+    c.take<__nv_bfloat16>((size_t)std::max<int64_t>(n, 1) * dp * 2);
+    c.take<__nv_bfloat16>((size_t)std::max<int64_t>(nq, 1) * dp * 2);
+    c.take<float>((size_t)(std::max<int64_t>(n, 1) + TC_N - 1) / TC_N * TC_N);
+    c.take<double>((size_t)std::max(d, 1));
+    c.take<float>((size_t)std::max(d, 1));
     return c.used;
 }
 
@@ -787,8 +1240,12 @@ extern "C" int onng_knn(const float *X, int64_t n, int32_t d, const float *Q, in
     unsigned long long *best = c.take<unsigned long long>((size_t)nq * kc);
     unsigned long long *bufp = c.take<unsigned long long>((size_t)nq * std::max(BUF, TC_BUF));
     int *flags = c.take<int>(64);
-    __nv_bfloat16 *xb = c.take<__nv_bfloat16>((size_t)std::max<int64_t>(n, 1) * d);
-    __nv_bfloat16 *qb = c.take<__nv_bfloat16>((size_t)nq * d);
+    const size_t dp = (size_t)(d + 63) / 64 * 64;
+    __nv_bfloat16 *xb = c.take<__nv_bfloat16>((size_t)std::max<int64_t>(n, 1) * dp * 2);
+    __nv_bfloat16 *qb = c.take<__nv_bfloat16>((size_t)nq * dp * 2);
+    float *xh = c.take<float>((size_t)(std::max<int64_t>(n, 1) + TC_N - 1) / TC_N * TC_N);
+    double *sums = c.take<double>((size_t)d);
+    float *mu = c.take<float>((size_t)d);
     cudaStream_t s = to_cuda(stream);
     if (n > 0)
         norms_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(X, n, d, xn);
@@ -796,17 +1253,24 @@ extern "C" int onng_knn(const float *X, int64_t n, int32_t d, const float *Q, in
     int st = check_launch("onng_knn: norms");
     if (st)
         return st;
-    // tensor-core path: d of 64 or 128, k + 16 <= 128, byte-valued inputs
-    if (n > 0 && (d == 64 || d == 128) && kc <= 128 && n <= INT32_MAX - TC_N) {
+    // tensor-core paths (at least one full tile of base rows and one row block of
+    // queries, k + 16 <= 128): byte-valued inputs at d = 64 / 128 exactly; other
+    // non-integer inputs at d >= 32 by the split bfloat16 form.  Integer-valued
+    // inputs otherwise take the SIMT sweep, which ranks them exactly.
+    if (n >= TC_N && nq >= TC_M && kc <= 128 && n <= INT32_MAX - TC_N) {
         ONNG_CUDA_TRY(cudaMemsetAsync(flags, 0, 64 * sizeof(int), s), "onng_knn: clear flags");
         const int gb = num_sms() * 8;
-        bf16_exact_kernel<<<gb, 256, 0, s>>>(X, n * d, flags);
-        bf16_exact_kernel<<<gb, 256, 0, s>>>(Q, nq * d, flags);
-        int inexact = 1;
-        ONNG_CUDA_TRY(cudaMemcpyAsync(&inexact, flags, sizeof(int), cudaMemcpyDeviceToHost, s), "onng_knn: flag");
-        ONNG_CUDA_TRY(cudaStreamSynchronize(s), "onng_knn: exactness check");
-        if (!inexact)
-            return launch_tc(X, n, d, Q, nq, k, kc, self_offset, nbr, len, xn, qn, best, bufp, flags + 1, xb, qb, s);
+        value_kind_kernel<<<gb, 256, 0, s>>>(X, n * d, flags);
+        value_kind_kernel<<<gb, 256, 0, s>>>(Q, nq * d, flags);
+        int kind = 3;
+        ONNG_CUDA_TRY(cudaMemcpyAsync(&kind, flags, sizeof(int), cudaMemcpyDeviceToHost, s), "onng_knn: flag");
+        ONNG_CUDA_TRY(cudaStreamSynchronize(s), "onng_knn: value check");
+        if (!(kind & 1) && (d == 64 || d == 128))
+            return launch_tc(X, n, d, Q, nq, k, kc, self_offset, nbr, len, xn, xh, qn, best, bufp, flags + 1, xb,
+                             qb, s);
+        if ((kind & 2) && d >= 32)
+            return launch_tcs(X, n, d, Q, nq, k, kc, self_offset, nbr, len, xh, qn, best, bufp, flags + 1, xb, qb,
+                              sums, mu, s);
     }
     switch (kc) {
     case 32: return launch<32>(X, n, d, Q, nq, k, self_offset, nbr, len, xn, qn, best, bufp, s);

@@ -73,7 +73,8 @@ def test_knng_tensor_core_ties(onng, d):
 
 
 def test_knn_tensor_core_ragged_and_self(onng):
-    """Row and column counts that are not multiples of the 128 x 256 tile, queries
+    """Row and column counts that are not multiples of the tile (256 query rows in
+    two blocks of 128, 128 base columns), a last CTA with one row block, queries
     that are base rows (self excluded) and queries that are not."""
     X, Q = synth.workload("sift1m", n=1000 + 77, nq=131)
     ids, ln = onng.knn(dev(X), dev(X[300:300 + 131]), 17, self_offset=300)
@@ -89,6 +90,31 @@ def test_knng_float_near_ties_only(onng):
     nbr, ln = onng.build_knng(dev(X), 40)
     o_ids, o_len = oracle.knng(X, 40)
     assert_rows_match(host(nbr), host(ln), o_ids, o_len, exact=False)
+
+
+def test_knng_float_split_tensor_core_offset(onng):
+    """Float data far from the origin (every coordinate + 1000) takes the split
+    bfloat16 tensor-core sweep, which centres both sets on the base mean first:
+    the ranking error scales with the spread of the data, not with its offset."""
+    X, _ = synth.workload("gmm10k", n=3000, nq=1)
+    X = (X + 1000.0).astype(np.float32)
+    nbr, ln = onng.build_knng(dev(X), 40)
+    o_ids, o_len = oracle.knng(X, 40)
+    assert_rows_match(host(nbr), host(ln), o_ids, o_len, exact=False)
+
+
+def test_knn_float_simt_sweep(onng):
+    """Float inputs below the tensor-core paths' sizes (d < 32; fewer than 128
+    queries) take the float32 SIMT sweep."""
+    rng = np.random.default_rng(5)
+    X = rng.random((2500, 16), dtype=np.float32)
+    nbr, ln = onng.build_knng(dev(X), 20)
+    o_ids, o_len = oracle.knng(X, 20)
+    assert_rows_match(host(nbr), host(ln), o_ids, o_len, exact=False)
+    Xg, Qg = synth.workload("gmm10k", n=3000, nq=60)
+    ids, ln = onng.knn(dev(Xg), dev(Qg), 10)
+    o_ids, o_len = oracle.knn(Xg, Qg, 10)
+    assert_rows_match(host(ids), host(ln), o_ids, o_len, exact=False)
 
 
 def test_knn_queries_ground_truth(onng):

@@ -2,8 +2,8 @@
 
 The search kernels read a vector as float4 chunks, one per lane and round:
 d = 100 leaves a ragged last round (25 of 32 lanes), d = 960 takes eight rounds
-(240 chunks).  The kNN graph of float data at these d goes through the float32
-tile sweep.  Integer-valued inputs whose squared distances stay below 2^24 are
+(240 chunks).  The kNN graph of float data at these d goes through the split
+bfloat16 tensor-core sweep (queries fewer than 128: the float32 SIMT sweep).  Integer-valued inputs whose squared distances stay below 2^24 are
 exact in float32, so there graphs and searches must equal the float64 oracle bit
 for bit at every eps; float inputs follow the near-tie rules of parity_helpers.
 
