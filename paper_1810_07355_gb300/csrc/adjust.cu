@@ -212,6 +212,7 @@ __global__ void unpack_keys(const unsigned long long *__restrict__ keys, const i
 constexpr int kPathSmall = 256;       // rows up to this many edges: one warp, shared-memory hash
 constexpr int kPathHash = 512;        // hash slots for small rows
 constexpr int kPathWarps = 4;
+constexpr int kPathUnroll = 4;  // list entries per lane in flight
 
 struct PathSmem {
     int hkey[kPathHash];
@@ -280,9 +281,19 @@ __device__ void path_row_warp(int64_t i, const int64_t *__restrict__ rp, const i
         const int u = u0 + lane;
         int64_t cnt = 0, mb = 0;
         if (u < deg && sm.li[u] < lmax) {
+            // only the prefix of m's list shorter than lmax can witness (rows are
+            // sorted by length): its size by binary search
             const int m = col[beg + u];
             mb = rp[m];
-            cnt = rp[m + 1] - mb;
+            int64_t lo = 0, hi = rp[m + 1] - mb;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (len[mb + mid] < lmax)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            cnt = lo;
         }
         int64_t x = cnt;
 #pragma unroll
@@ -296,28 +307,45 @@ __device__ void path_row_warp(int64_t i, const int64_t *__restrict__ rp, const i
         sm.mu[lane] = u;
         __syncwarp();
         const int64_t total = sm.pre[31];
-        for (int64_t e = lane; e < total; e += 32) {
-            int lo = 0, hi = 31;  // first lane whose inclusive prefix exceeds e
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (sm.pre[mid] > e)
-                    hi = mid;
-                else
-                    lo = mid + 1;
+        // kPathUnroll entries per lane and round: their list loads are all issued
+        // before any is used, so several gathers are in flight per lane
+        for (int64_t e0 = lane; e0 < total; e0 += 32 * kPathUnroll) {
+            int own[kPathUnroll];
+            int64_t idx[kPathUnroll];
+#pragma unroll
+            for (int r = 0; r < kPathUnroll; ++r) {
+                const int64_t e = e0 + 32 * r;
+                int lo = 0, hi = 31;  // first lane whose inclusive prefix exceeds e
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (sm.pre[mid] > e)
+                        hi = mid;
+                    else
+                        lo = mid + 1;
+                }
+                own[r] = e < total ? lo : -1;
+                const int64_t start = sm.pre[lo] - (lo ? sm.pre[lo - 1] : 0);
+                idx[r] = sm.mb[lo] + (e - (sm.pre[lo] - start));
             }
-            const int64_t start = sm.pre[lo] - (lo ? sm.pre[lo - 1] : 0);
-            const int64_t off = e - (sm.pre[lo] - start);
-            const int64_t idx = sm.mb[lo] + off;
-            const float lmj = len[idx];
-            if (!(lmj < lmax))
-                continue;
-            const int t = hash_find(sm.hkey, sm.hpos, kPathHash, lg, col[idx]);
-            if (t < 0)
-                continue;
-            const int uu = sm.mu[lo];
-            const float lij = sm.li[t];
-            if (sm.li[uu] < lij && lmj < lij)
-                atomicMin(&sm.wit[t], uu);
+            float lmj[kPathUnroll];
+            int cj[kPathUnroll];
+#pragma unroll
+            for (int r = 0; r < kPathUnroll; ++r) {
+                lmj[r] = own[r] >= 0 ? len[idx[r]] : INFINITY;
+                cj[r] = own[r] >= 0 ? col[idx[r]] : -1;
+            }
+#pragma unroll
+            for (int r = 0; r < kPathUnroll; ++r) {
+                if (own[r] < 0 || !(lmj[r] < lmax))
+                    continue;
+                const int t = hash_find(sm.hkey, sm.hpos, kPathHash, lg, cj[r]);
+                if (t < 0)
+                    continue;
+                const int uu = sm.mu[own[r]];
+                const float lij = sm.li[t];
+                if (sm.li[uu] < lij && lmj[r] < lij)
+                    atomicMin(&sm.wit[t], uu);
+            }
         }
         __syncwarp();
     }

@@ -298,7 +298,7 @@ __global__ void knn_final_kernel(const float *__restrict__ X, int d, const float
 // when its TMEM reads are done and merges afterwards.  Every mbarrier wait gives
 // up after 2 s, records an error code and lets all roles reach the teardown,
 // where TMEM is freed.
-constexpr int TC_M = 128, TC_N = 128, TC_BUF = 256, TC_STAGES = 3;
+constexpr int TC_M = 128, TC_N = 128, TC_BUF = 256;
 constexpr int TC_RB = 2;                    // 128-row blocks per CTA
 constexpr int TC_ROWS = TC_M * TC_RB;       // query rows per CTA
 constexpr int TC_EPI = 256;                 // epilogue threads (8 warps), one per row
@@ -414,8 +414,9 @@ template <int KA> struct TcSmem {
     static constexpr int B_ATOM = TC_N * 128;
     static constexpr int A_BYTES = TC_RB * KA * A_ATOM;
     static constexpr int B_STAGE = KA * B_ATOM;
+    static constexpr int STAGES = KA >= 3 ? 2 : 3;  // the B ring within 227 KB
     // alignment slack, operands, then barriers and the TMEM address
-    static constexpr int BYTES = 1024 + A_BYTES + TC_STAGES * B_STAGE + 256;
+    static constexpr int BYTES = 1024 + A_BYTES + STAGES * B_STAGE + 256;
 };
 
 // Compact warp sorts for the tensor-core epilogue: the stage loops run at run
@@ -489,9 +490,9 @@ template <int N> __device__ void warp_merge_compact(unsigned long long (&v)[N], 
 }
 
 // The warp merges row gr's cnt buffered keys into its sorted best list of KC
-// keys and returns the new threshold (the KC-th distance).
+// keys and returns the new threshold: the distance of list entry kth (< KC).
 template <int KC>
-__device__ __noinline__ float tc_merge_row(int64_t gr, int cnt, unsigned long long *__restrict__ best,
+__device__ __noinline__ float tc_merge_row(int64_t gr, int cnt, int kth, unsigned long long *__restrict__ best,
                                            const unsigned long long *__restrict__ buf, int lane)
 {
     static_assert(KC <= TC_BUF && TC_BUF == 256, "the buffer sort holds 256 keys");
@@ -518,7 +519,11 @@ __device__ __noinline__ float tc_merge_row(int64_t gr, int cnt, unsigned long lo
 #pragma unroll
     for (int i = 0; i < PB; ++i)
         best[gr * KC + i * 32 + lane] = m[i];
-    return key_dist(__shfl_sync(0xffffffffu, m[PB - 1], 31));
+    unsigned long long kv = m[0];
+#pragma unroll
+    for (int i = 1; i < PB; ++i)
+        kv = (kth >> 5) == i ? m[i] : kv;
+    return key_dist(__shfl_sync(0xffffffffu, kv, kth & 31));
 }
 
 // a[j] for a run-time j in [0, 32): a five-level select tree (no local memory)
@@ -612,14 +617,66 @@ __device__ __forceinline__ void tc_chunk(const uint32_t (&v)[32], const float4 (
     }
 }
 
+// The byte-valued form of a chunk: the accumulator already holds
+// v = q.x - floor(|x|^2 / 2) (the MMA adds the spare K atom's pieces), an integer,
+// and v >= q.x - |x|^2 / 2, so v >= tr selects a superset of the hits; a passing
+// lane corrects each candidate by the parity of |x|^2 (one bit per column in
+// par, loaded only here) to a = q.x - |x|^2 / 2 and keeps it when a >= tr, i.e.
+// d^2 <= thr.  The comparison is not strict because thr is the k-th distance so
+// far here (ranking is exact, so the list needs no slack): a later column at that
+// distance may still win its tie by id.  Columns past n (zero rows of the last
+// tile) are skipped.
+__device__ __forceinline__ void tc_chunk_aug(const uint32_t (&v)[32], float tr, float qnr, int64_t cb, int64_t self,
+                                             int64_t n, const unsigned *__restrict__ par,
+                                             unsigned long long *__restrict__ brow, int &cnt)
+{
+    const float *f = reinterpret_cast<const float *>(v);
+    float m[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        m[i] = f[i];
+#pragma unroll
+    for (int j = 8; j < 32; j += 8)
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            m[i] = fmaxf(m[i], f[j + i]);
+    const float mx = fmaxf(fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3])), fmaxf(fmaxf(m[4], m[5]), fmaxf(m[6], m[7])));
+    if (!(mx >= tr))
+        return;
+    float a[32];
+    unsigned hit = 0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        a[j] = f[j];
+        hit |= (a[j] >= tr ? 1u : 0u) << j;
+    }
+    const int64_t sj = self - cb;
+    if (sj >= 0 && sj < 32)
+        hit &= ~(1u << (int)sj);
+    if (n - cb < 32)
+        hit &= n - cb > 0 ? (1u << (int)(n - cb)) - 1u : 0u;
+    if (!hit)
+        return;
+    const unsigned odd = __ldg(par + (cb >> 5));
+    while (hit) {
+        const int j = __ffs(hit) - 1;
+        hit &= hit - 1;
+        const float aj = pick32(a, j) - ((odd >> j) & 1u ? 0.5f : 0.f);
+        if (aj >= tr)
+            brow[cnt++] = pack_key(fmaxf(qnr - 2.f * aj, 0.f), (int)(cb + j));
+    }
+}
+
 // The epilogue of the tensor-core kernels (warps 0-7; see knn_tc_kernel): one
 // query row per thread, tile by tile from the TMEM accumulators (row block rb =
 // warp / 4 at columns (2 rb + b) * TC_N, b = tile & 1).
-template <int KC>
+// AUG: the byte-valued form (tc_chunk_aug with the parity bits `par`); otherwise
+// the split float form (tc_chunk with the padded half norms `xh`).
+template <int KC, bool AUG>
 __device__ void tc_epilogue(uint64_t *accf, uint64_t *acce, uint32_t tmem, int warp, int lane, int64_t row0,
-                            int64_t nq, int64_t tiles, int64_t self_offset, const float *__restrict__ xh,
-                            const float *__restrict__ qn, unsigned long long *__restrict__ best,
-                            unsigned long long *__restrict__ buf, int *err)
+                            int64_t nq, int64_t n, int64_t tiles, int kth, int64_t self_offset, const float *__restrict__ xh,
+                            const unsigned *__restrict__ par, const float *__restrict__ qn,
+                            unsigned long long *__restrict__ best, unsigned long long *__restrict__ buf, int *err)
 {
     const int rb = warp >> 2, qd = warp & 3;
     const int64_t grow = row0 + rb * TC_M + qd * 32 + lane;
@@ -651,13 +708,21 @@ __device__ void tc_epilogue(uint64_t *accf, uint64_t *acce, uint32_t tmem, int w
 #pragma unroll 1
         for (int c = 0; c < TC_N / 32; c += 2) {
             tmem_ld32_async(tb + (uint32_t)((c + 1) * 32), vb);
-            load_h(hq, h4 + c * 8);
-            tc_chunk(va, hq, tr, qnr, col0 + c * 32, self, brow, cnt);
+            if constexpr (AUG) {
+                tc_chunk_aug(va, tr, qnr, col0 + c * 32, self, n, par, brow, cnt);
+            } else {
+                load_h(hq, h4 + c * 8);
+                tc_chunk(va, hq, tr, qnr, col0 + c * 32, self, brow, cnt);
+            }
             tmem_wait32(vb);
             if (c + 2 < TC_N / 32)
                 tmem_ld32_async(tb + (uint32_t)((c + 2) * 32), va);
-            load_h(hq, h4 + (c + 1) * 8);
-            tc_chunk(vb, hq, tr, qnr, col0 + (c + 1) * 32, self, brow, cnt);
+            if constexpr (AUG) {
+                tc_chunk_aug(vb, tr, qnr, col0 + (c + 1) * 32, self, n, par, brow, cnt);
+            } else {
+                load_h(hq, h4 + (c + 1) * 8);
+                tc_chunk(vb, hq, tr, qnr, col0 + (c + 1) * 32, self, brow, cnt);
+            }
             if (c + 2 < TC_N / 32)
                 tmem_wait32(va);
         }
@@ -671,7 +736,7 @@ __device__ void tc_epilogue(uint64_t *accf, uint64_t *acce, uint32_t tmem, int w
             need &= need - 1;
             const int64_t gr = __shfl_sync(0xffffffffu, grow, src);
             const int c = __shfl_sync(0xffffffffu, cnt, src);
-            const float nt = tc_merge_row<KC>(gr, c, best, buf, lane);
+            const float nt = tc_merge_row<KC>(gr, c, kth, best, buf, lane);
             if (lane == src) {
                 thr = nt;
                 cnt = 0;
@@ -683,7 +748,7 @@ __device__ void tc_epilogue(uint64_t *accf, uint64_t *acce, uint32_t tmem, int w
 template <int KC, int KA>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n,
-                  int64_t nq, int64_t self_offset, const float *__restrict__ xh, const float *__restrict__ qn,
+                  int64_t nq, int k, int64_t self_offset, const unsigned *__restrict__ par, const float *__restrict__ qn,
                   unsigned long long *__restrict__ best, unsigned long long *__restrict__ buf, int *err)
 {
     using L = TcSmem<KA>;
@@ -691,8 +756,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *sA = base;
     unsigned char *sB = base + L::A_BYTES;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + TC_STAGES * L::B_STAGE);
-    uint64_t *full = bars, *empty = bars + TC_STAGES, *accf = bars + 2 * TC_STAGES, *acce = accf + 2, *abar = acce + 2;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + L::STAGES * L::B_STAGE);
+    uint64_t *full = bars, *empty = bars + L::STAGES, *accf = bars + 2 * L::STAGES, *acce = accf + 2, *abar = acce + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(abar + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -701,7 +766,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int nrb = row0 + TC_M < nq ? TC_RB : 1;  // row blocks holding any query row
 
     if (tid == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < L::STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -736,8 +801,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 for (int a = 0; a < KA; ++a)
                     tma_load_2d(sA + (rb * KA + a) * L::A_ATOM, &tmA, a * 64, (int)(row0 + rb * TC_M), abar);
             for (int64_t t = 0; t < tiles; ++t) {
-                const int s = (int)(t % TC_STAGES);
-                if (t >= TC_STAGES && !mbar_wait(&empty[s], (uint32_t)(((t / TC_STAGES) & 1) ^ 1), err, 1))
+                const int s = (int)(t % L::STAGES);
+                if (t >= L::STAGES && !mbar_wait(&empty[s], (uint32_t)(((t / L::STAGES) & 1) ^ 1), err, 1))
                     break;
                 mbar_expect_tx(&full[s], L::B_STAGE);
                 for (int a = 0; a < KA; ++a)
@@ -746,8 +811,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             // our copies in flight complete before the CTA may exit (bounded)
             mbar_drain(abar, 0, err, 6);
-            for (int64_t t = issued > TC_STAGES ? issued - TC_STAGES : 0; t < issued; ++t)
-                mbar_drain(&full[t % TC_STAGES], (uint32_t)((t / TC_STAGES) & 1), err, 6);
+            for (int64_t t = issued > L::STAGES ? issued - L::STAGES : 0; t < issued; ++t)
+                mbar_drain(&full[t % L::STAGES], (uint32_t)((t / L::STAGES) & 1), err, 6);
         }
     } else if (warp == 9) {
         // ------------------------------------------------ MMA issuer
@@ -756,8 +821,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int64_t done = 0;
             bool ok = mbar_wait(abar, 0, err, 2);
             for (int64_t t = 0; ok && t < tiles; ++t) {
-                const int s = (int)(t % TC_STAGES), b = (int)(t & 1);
-                if (!mbar_wait(&full[s], (uint32_t)((t / TC_STAGES) & 1), err, 3))
+                const int s = (int)(t % L::STAGES), b = (int)(t & 1);
+                if (!mbar_wait(&full[s], (uint32_t)((t / L::STAGES) & 1), err, 3))
                     break;
                 if (t >= 2 && !mbar_wait(&acce[b], (uint32_t)(((t >> 1) & 1) ^ 1), err, 4))
                     break;
@@ -786,7 +851,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else {
         // ------------------------------------------------ epilogue (warps 0-7)
-        tc_epilogue<KC>(accf, acce, tmem, warp, lane, row0, nq, tiles, self_offset, xh, qn, best, buf, err);
+        tc_epilogue<KC, true>(accf, acce, tmem, warp, lane, row0, nq, n, tiles, k - 1, self_offset, nullptr, par, qn,
+                              best, buf, err);
     }
     tc_fence_before();
     __syncthreads();
@@ -933,7 +999,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else {
         // ------------------------------------------------ epilogue (warps 0-7)
-        tc_epilogue<KC>(accf, acce, tmem, warp, lane, row0, nq, tiles, self_offset, xh, qn, best, buf, err);
+        tc_epilogue<KC, false>(accf, acce, tmem, warp, lane, row0, nq, n, tiles, KC - 1, self_offset, xh, nullptr, qn,
+                               best, buf, err);
     }
     tc_fence_before();
     __syncthreads();
@@ -995,14 +1062,6 @@ __global__ void split_rows_kernel(const float *__restrict__ M, int64_t rows, int
     }
 }
 
-// xh[i] = |x_i|^2 / 2 for i < n, +inf up to the padded length (no column past n
-// can pass the threshold test).
-__global__ void half_norms_kernel(const float *__restrict__ xn, int64_t n, int64_t padded, float *__restrict__ xh)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < padded; i += (int64_t)gridDim.x * blockDim.x)
-        xh[i] = i < n ? 0.5f * xn[i] : INFINITY;
-}
-
 // Sets bit 0 of *flag if any value is not an integer in [0, 255] (byte-valued
 // descriptors: exact in bfloat16, and at d <= 128 every squared norm, dot product,
 // |x|^2 / 2 and distance of the tensor-core path is an exact float32 below 2^23),
@@ -1021,10 +1080,44 @@ __global__ void value_kind_kernel(const float *__restrict__ x, int64_t count, in
         atomicOr(flag, (int)bad);
 }
 
-__global__ void f32_to_bf16_kernel(const float *__restrict__ x, int64_t count, __nv_bfloat16 *__restrict__ y)
+// The byte-valued form's operands: row r of M in bfloat16 in columns [0, d) of a
+// row of dpa = d + 64 (an extra K atom), then in columns d, d + 1, d + 2 either
+// 1.0 (queries: s == nullptr) or the three pieces of -floor(s_r / 2) (base rows;
+// s_r = |x_r|^2, an integer below 2^23): its 8-bit fields times 2^16, 2^8 and 1,
+// each exact in bfloat16; zeros elsewhere.  The MMA then accumulates
+// q.x - floor(|x|^2 / 2) exactly.
+__global__ void aug_rows_kernel(const float *__restrict__ M, int64_t rows, int d, int dpa,
+                                const float *__restrict__ s, __nv_bfloat16 *__restrict__ out)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = __float2bfloat16_rn(x[i]);
+    const int lane = threadIdx.x & 31;
+    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < rows;
+         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const unsigned h = s ? ((unsigned)s[r]) >> 1 : 0u;
+        for (int j = lane; j < dpa; j += 32) {
+            float v = 0.f;
+            if (j < d)
+                v = M[r * d + j];
+            else if (j < d + 3) {
+                const int p = j - d;
+                v = !s ? 1.f : -(float)(p == 0 ? (h >> 16) << 16 : p == 1 ? ((h >> 8) & 255u) << 8 : h & 255u);
+            }
+            out[r * dpa + j] = __float2bfloat16_rn(v);
+        }
+    }
+}
+
+// Bit i of par = the parity of the integer s_i (0 past n), one word per 32 columns.
+__global__ void parity_kernel(const float *__restrict__ s, int64_t n, int64_t words, unsigned *__restrict__ par)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < words;
+         w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t i = w * 32 + lane;
+        const unsigned bit = i < n ? ((unsigned)s[i] & 1u) : 0u;
+        const unsigned b = __ballot_sync(0xffffffffu, bit != 0);
+        if (lane == 0)
+            par[w] = b;
+    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -1081,8 +1174,8 @@ int launch(const float *X, int64_t n, int d, const float *Q, int64_t nq, int k, 
 }
 
 template <int KC, int KA>
-int launch_tc_kc(const CUtensorMap &ma, const CUtensorMap &mb, int64_t n, int64_t nq, int64_t self_offset,
-                 const float *xh, const float *qn, unsigned long long *best, unsigned long long *bufp, int *err,
+int launch_tc_kc(const CUtensorMap &ma, const CUtensorMap &mb, int64_t n, int64_t nq, int k, int64_t self_offset,
+                 const unsigned *par, const float *qn, unsigned long long *best, unsigned long long *bufp, int *err,
                  cudaStream_t s)
 {
     const size_t smem = TcSmem<KA>::BYTES;
@@ -1090,34 +1183,35 @@ int launch_tc_kc(const CUtensorMap &ma, const CUtensorMap &mb, int64_t n, int64_
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                   "onng_knn: tensor kernel smem attribute");
     knn_tc_kernel<KC, KA><<<(unsigned)((nq + TC_ROWS - 1) / TC_ROWS), TC_THREADS, smem, s>>>(
-        ma, mb, n, nq, self_offset, xh, qn, best, bufp, err);
+        ma, mb, n, nq, k, self_offset, par, qn, best, bufp, err);
     return check_launch("onng_knn: tensor kernel");
 }
 
 int launch_tc(const float *X, int64_t n, int d, const float *Q, int64_t nq, int k, int kc, int64_t self_offset,
-              int32_t *nbr, float *len, const float *xn, float *xh, float *qn, unsigned long long *best,
+              int32_t *nbr, float *len, const float *xn, unsigned *par, float *qn, unsigned long long *best,
               unsigned long long *bufp, int *err, __nv_bfloat16 *xb, __nv_bfloat16 *qb, cudaStream_t s)
 {
     const int gb = num_sms() * 8;
-    f32_to_bf16_kernel<<<gb, 256, 0, s>>>(X, n * d, xb);
-    f32_to_bf16_kernel<<<gb, 256, 0, s>>>(Q, nq * d, qb);
-    half_norms_kernel<<<gb, 256, 0, s>>>(xn, n, (n + TC_N - 1) / TC_N * TC_N, xh);
-    int st = check_launch("onng_knn: bf16 copies");
+    const int dpa = d + 64;  // the extra K atom carries -floor(|x|^2 / 2)
+    aug_rows_kernel<<<gb, 256, 0, s>>>(X, n, d, dpa, xn, xb);
+    aug_rows_kernel<<<gb, 256, 0, s>>>(Q, nq, d, dpa, nullptr, qb);
+    parity_kernel<<<gb, 256, 0, s>>>(xn, n, (n + TC_N - 1) / TC_N * (TC_N / 32), par);
+    int st = check_launch("onng_knn: bf16 operands");
     if (st)
         return st;
     CUtensorMap ma, mb;
-    if ((st = make_map(&ma, qb, nq, d, TC_M)) || (st = make_map(&mb, xb, n, d, TC_N)))
+    if ((st = make_map(&ma, qb, nq, dpa, TC_M)) || (st = make_map(&mb, xb, n, dpa, TC_N)))
         return st;
-    const int ka = d / 64;
+    const int ka = dpa / 64;
     if (kc == 32)
-        st = ka == 1 ? launch_tc_kc<32, 1>(ma, mb, n, nq, self_offset, xh, qn, best, bufp, err, s)
-                     : launch_tc_kc<32, 2>(ma, mb, n, nq, self_offset, xh, qn, best, bufp, err, s);
+        st = ka == 2 ? launch_tc_kc<32, 2>(ma, mb, n, nq, k, self_offset, par, qn, best, bufp, err, s)
+                     : launch_tc_kc<32, 3>(ma, mb, n, nq, k, self_offset, par, qn, best, bufp, err, s);
     else if (kc == 64)
-        st = ka == 1 ? launch_tc_kc<64, 1>(ma, mb, n, nq, self_offset, xh, qn, best, bufp, err, s)
-                     : launch_tc_kc<64, 2>(ma, mb, n, nq, self_offset, xh, qn, best, bufp, err, s);
+        st = ka == 2 ? launch_tc_kc<64, 2>(ma, mb, n, nq, k, self_offset, par, qn, best, bufp, err, s)
+                     : launch_tc_kc<64, 3>(ma, mb, n, nq, k, self_offset, par, qn, best, bufp, err, s);
     else
-        st = ka == 1 ? launch_tc_kc<128, 1>(ma, mb, n, nq, self_offset, xh, qn, best, bufp, err, s)
-                     : launch_tc_kc<128, 2>(ma, mb, n, nq, self_offset, xh, qn, best, bufp, err, s);
+        st = ka == 2 ? launch_tc_kc<128, 2>(ma, mb, n, nq, k, self_offset, par, qn, best, bufp, err, s)
+                     : launch_tc_kc<128, 3>(ma, mb, n, nq, k, self_offset, par, qn, best, bufp, err, s);
     if (st)
         return st;
     int code = 0;
@@ -1208,13 +1302,14 @@ extern "C" size_t onng_knn_workspace_bytes(int64_t n, int32_t d, int64_t nq, int
     c.take<unsigned long long>((size_t)std::max<int64_t>(nq, 1) * (kc ? kc : 32));
     c.take<unsigned long long>((size_t)std::max<int64_t>(nq, 1) * std::max(BUF, TC_BUF));
     c.take<int>(64);
-    // bfloat16 copies: hi and lo rows of dp = 64 ceil(d / 64) (the byte path uses the hi half)
+    // bfloat16 copies: hi and lo rows of dp = 64 ceil(d / 64) (the byte path's rows of d + 64 fit)
     const size_t dp = (size_t)(std::max(d, 1) + 63) / 64 * 64;
     c.take<__nv_bfloat16>((size_t)std::max<int64_t>(n, 1) * dp * 2);
     c.take<__nv_bfloat16>((size_t)std::max<int64_t>(nq, 1) * dp * 2);
     c.take<float>((size_t)(std::max<int64_t>(n, 1) + TC_N - 1) / TC_N * TC_N);
     c.take<double>((size_t)std::max(d, 1));
     c.take<float>((size_t)std::max(d, 1));
+    c.take<unsigned>((size_t)(std::max<int64_t>(n, 1) + TC_N - 1) / TC_N * (TC_N / 32));
     return c.used;
 }
 
@@ -1246,6 +1341,7 @@ extern "C" int onng_knn(const float *X, int64_t n, int32_t d, const float *Q, in
     float *xh = c.take<float>((size_t)(std::max<int64_t>(n, 1) + TC_N - 1) / TC_N * TC_N);
     double *sums = c.take<double>((size_t)d);
     float *mu = c.take<float>((size_t)d);
+    unsigned *par = c.take<unsigned>((size_t)(std::max<int64_t>(n, 1) + TC_N - 1) / TC_N * (TC_N / 32));
     cudaStream_t s = to_cuda(stream);
     if (n > 0)
         norms_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(X, n, d, xn);
@@ -1266,7 +1362,7 @@ extern "C" int onng_knn(const float *X, int64_t n, int32_t d, const float *Q, in
         ONNG_CUDA_TRY(cudaMemcpyAsync(&kind, flags, sizeof(int), cudaMemcpyDeviceToHost, s), "onng_knn: flag");
         ONNG_CUDA_TRY(cudaStreamSynchronize(s), "onng_knn: value check");
         if (!(kind & 1) && (d == 64 || d == 128))
-            return launch_tc(X, n, d, Q, nq, k, kc, self_offset, nbr, len, xn, xh, qn, best, bufp, flags + 1, xb,
+            return launch_tc(X, n, d, Q, nq, k, kc, self_offset, nbr, len, xn, par, qn, best, bufp, flags + 1, xb,
                              qb, s);
         if ((kind & 2) && d >= 32)
             return launch_tcs(X, n, d, Q, nq, k, kc, self_offset, nbr, len, xh, qn, best, bufp, flags + 1, xb, qb,
