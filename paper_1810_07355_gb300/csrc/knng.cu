@@ -409,14 +409,19 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar)
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// KA atoms per row: KA - 1 of data and the spare atom.  A holds the data atoms of
+// both row blocks and one spare atom (1.0 in its first three columns for every
+// row) that both blocks share; only its first K = 16 step is non-zero, so the MMA
+// takes that step alone.
 template <int KA> struct TcSmem {
     static constexpr int A_ATOM = TC_M * 128;   // bytes of one 64-wide K atom of a 128-row block
     static constexpr int B_ATOM = TC_N * 128;
-    static constexpr int A_BYTES = TC_RB * KA * A_ATOM;
+    static constexpr int A_BYTES = (TC_RB * (KA - 1) + 1) * A_ATOM;
     static constexpr int B_STAGE = KA * B_ATOM;
-    static constexpr int STAGES = KA >= 3 ? 2 : 3;  // the B ring within 227 KB
+    static constexpr int STAGES = 3;
     // alignment slack, operands, then barriers and the TMEM address
     static constexpr int BYTES = 1024 + A_BYTES + STAGES * B_STAGE + 256;
+    static_assert(BYTES <= 232448, "more than 227 KB of shared memory");
 };
 
 // Compact warp sorts for the tensor-core epilogue: the stage loops run at run
@@ -674,7 +679,8 @@ __device__ __forceinline__ void tc_chunk_aug(const uint32_t (&v)[32], float tr, 
 // the split float form (tc_chunk with the padded half norms `xh`).
 template <int KC, bool AUG>
 __device__ void tc_epilogue(uint64_t *accf, uint64_t *acce, uint32_t tmem, int warp, int lane, int64_t row0,
-                            int64_t nq, int64_t n, int64_t tiles, int kth, int64_t self_offset, const float *__restrict__ xh,
+                            int64_t nq, int64_t n, int64_t tiles, int64_t t0, int kth, int64_t self_offset,
+                            const float *__restrict__ xh,
                             const unsigned *__restrict__ par, const float *__restrict__ qn,
                             unsigned long long *__restrict__ best, unsigned long long *__restrict__ buf, int *err)
 {
@@ -693,7 +699,7 @@ __device__ void tc_epilogue(uint64_t *accf, uint64_t *acce, uint32_t tmem, int w
         if (!__all_sync(0xffffffffu, ok))
             break;
         tc_fence_after();
-        const int64_t col0 = t * TC_N;
+        const int64_t col0 = ((t + t0) % tiles) * TC_N;
         // d^2 = |q|^2 + |x|^2 - 2 q.x < thr  <=>  q.x - |x|^2 / 2 > (|q|^2 - thr) / 2, every
         // term an exact integer or half-integer for byte-valued inputs (approximate in
         // the split float form, whose survivors are rescored)
@@ -764,6 +770,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int64_t row0 = (int64_t)blockIdx.x * TC_ROWS;
     const int64_t tiles = (n + TC_N - 1) / TC_N;
     const int nrb = row0 + TC_M < nq ? TC_RB : 1;  // row blocks holding any query row
+    // a self-join starts its sweep at the tile of its own rows and wraps around:
+    // where nearby rows sit together, the thresholds fall within the first tiles
+    const int64_t t0 = self_offset >= 0 ? ((self_offset + row0) / TC_N) % tiles : 0;
 
     if (tid == 0) {
         for (int s = 0; s < L::STAGES; ++s) {
@@ -796,17 +805,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
             int64_t issued = 0;
-            mbar_expect_tx(abar, nrb * KA * L::A_ATOM);
+            mbar_expect_tx(abar, (nrb * (KA - 1) + 1) * L::A_ATOM);
             for (int rb = 0; rb < nrb; ++rb)
-                for (int a = 0; a < KA; ++a)
-                    tma_load_2d(sA + (rb * KA + a) * L::A_ATOM, &tmA, a * 64, (int)(row0 + rb * TC_M), abar);
+                for (int a = 0; a < KA - 1; ++a)
+                    tma_load_2d(sA + (rb * (KA - 1) + a) * L::A_ATOM, &tmA, a * 64, (int)(row0 + rb * TC_M), abar);
+            // the spare atom from block 0's rows: a valid row of block 1 sits 128 rows
+            // past a valid row of block 0, and all valid rows carry the same 1.0s
+            tma_load_2d(sA + TC_RB * (KA - 1) * L::A_ATOM, &tmA, (KA - 1) * 64, (int)row0, abar);
             for (int64_t t = 0; t < tiles; ++t) {
                 const int s = (int)(t % L::STAGES);
                 if (t >= L::STAGES && !mbar_wait(&empty[s], (uint32_t)(((t / L::STAGES) & 1) ^ 1), err, 1))
                     break;
                 mbar_expect_tx(&full[s], L::B_STAGE);
                 for (int a = 0; a < KA; ++a)
-                    tma_load_2d(sB + s * L::B_STAGE + a * L::B_ATOM, &tmB, a * 64, (int)(t * TC_N), &full[s]);
+                    tma_load_2d(sB + s * L::B_STAGE + a * L::B_ATOM, &tmB, a * 64, (int)(((t + t0) % tiles) * TC_N),
+                                &full[s]);
                 issued = t + 1;
             }
             // our copies in flight complete before the CTA may exit (bounded)
@@ -832,14 +845,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 for (int rb = 0; rb < TC_RB; ++rb) {
                     if (rb >= nrb)
                         break;
-                    const uint32_t aa = smem_u32(sA + rb * KA * L::A_ATOM);
+                    const uint32_t aa = smem_u32(sA + rb * (KA - 1) * L::A_ATOM);
+                    const uint32_t dt = tmem + (uint32_t)((rb * 2 + b) * TC_N);
 #pragma unroll
-                    for (int kk = 0; kk < 4 * KA; ++kk) {
+                    for (int kk = 0; kk < 4 * (KA - 1); ++kk) {
                         const uint32_t off = (uint32_t)((kk & 3) * 32);  // 16 bf16 = 32 bytes inside the atom
                         const uint64_t ad = umma_desc(aa + (kk >> 2) * L::A_ATOM + off);
                         const uint64_t bd = umma_desc(bb + (kk >> 2) * L::B_ATOM + off);
-                        umma_bf16(tmem + (uint32_t)((rb * 2 + b) * TC_N), ad, bd, idesc, kk > 0 ? 1u : 0u);
+                        umma_bf16(dt, ad, bd, idesc, kk > 0 ? 1u : 0u);
                     }
+                    // the spare atom's first K step adds -floor(|x|^2 / 2)
+                    umma_bf16(dt, umma_desc(smem_u32(sA + TC_RB * (KA - 1) * L::A_ATOM)),
+                              umma_desc(bb + (KA - 1) * L::B_ATOM), idesc, 1u);
                 }
                 umma_commit(&empty[s]);
                 umma_commit(&accf[b]);
@@ -851,7 +868,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else {
         // ------------------------------------------------ epilogue (warps 0-7)
-        tc_epilogue<KC, true>(accf, acce, tmem, warp, lane, row0, nq, n, tiles, k - 1, self_offset, nullptr, par, qn,
+        tc_epilogue<KC, true>(accf, acce, tmem, warp, lane, row0, nq, n, tiles, t0, k - 1, self_offset, nullptr, par, qn,
                               best, buf, err);
     }
     tc_fence_before();
@@ -903,6 +920,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int64_t tiles = (n + TC_N - 1) / TC_N;
     const int64_t steps = tiles * nk;
     const int nrb = row0 + TC_M < nq ? TC_RB : 1;  // row blocks holding any query row
+    // a self-join starts its sweep at the tile of its own rows and wraps around:
+    // where nearby rows sit together, the thresholds fall within the first tiles
+    const int64_t t0 = self_offset >= 0 ? ((self_offset + row0) / TC_N) % tiles : 0;
 
     if (tid == 0) {
         for (int s = 0; s < TCS_STAGES; ++s) {
@@ -948,8 +968,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tma_load_2d(st + rb * L::ATOM, &tmAh, kc * 64, (int)(row0 + rb * TC_M), &full[s]);
                     tma_load_2d(st + (2 + rb) * L::ATOM, &tmAl, kc * 64, (int)(row0 + rb * TC_M), &full[s]);
                 }
-                tma_load_2d(st + 4 * L::ATOM, &tmBh, kc * 64, (int)(t * TC_N), &full[s]);
-                tma_load_2d(st + 5 * L::ATOM, &tmBl, kc * 64, (int)(t * TC_N), &full[s]);
+                tma_load_2d(st + 4 * L::ATOM, &tmBh, kc * 64, (int)(((t + t0) % tiles) * TC_N), &full[s]);
+                tma_load_2d(st + 5 * L::ATOM, &tmBl, kc * 64, (int)(((t + t0) % tiles) * TC_N), &full[s]);
                 issued = step + 1;
             }
             // our copies in flight complete before the CTA may exit (bounded)
@@ -999,7 +1019,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else {
         // ------------------------------------------------ epilogue (warps 0-7)
-        tc_epilogue<KC, false>(accf, acce, tmem, warp, lane, row0, nq, n, tiles, KC - 1, self_offset, xh, nullptr, qn,
+        tc_epilogue<KC, false>(accf, acce, tmem, warp, lane, row0, nq, n, tiles, t0, KC - 1, self_offset, xh, nullptr, qn,
                                best, buf, err);
     }
     tc_fence_before();
