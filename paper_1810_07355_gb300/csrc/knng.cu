@@ -300,6 +300,7 @@ __global__ void knn_final_kernel(const float *__restrict__ X, int d, const float
 // where TMEM is freed.
 constexpr int TC_M = 128, TC_N = 128, TC_BUF = 256;
 constexpr int TC_RB = 2;                    // 128-row blocks per CTA
+constexpr int TC_EAGER = 64;                // buffered keys that trigger a merge
 constexpr int TC_ROWS = TC_M * TC_RB;       // query rows per CTA
 constexpr int TC_EPI = 256;                 // epilogue threads (8 warps), one per row
 constexpr int TC_THREADS = TC_EPI + 64;     // + TMA warp + MMA warp
@@ -508,7 +509,21 @@ __device__ __noinline__ float tc_merge_row(int64_t gr, int cnt, int kth, unsigne
         const int e = i * 32 + lane;
         a[i] = e < cnt ? buf[gr * TC_BUF + e] : EMPTY_KEY;
     }
-    warp_sort_compact<8>(a, lane);
+    // sort the smallest power-of-two prefix holding the cnt keys (the rest is +inf)
+    if (cnt <= 64) {
+        unsigned long long t[2] = {a[0], a[1]};
+        warp_sort_compact<2>(t, lane);
+        a[0] = t[0];
+        a[1] = t[1];
+    } else if (cnt <= 128) {
+        unsigned long long t[4] = {a[0], a[1], a[2], a[3]};
+        warp_sort_compact<4>(t, lane);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            a[i] = t[i];
+    } else {
+        warp_sort_compact<8>(a, lane);
+    }
     unsigned long long bv[PB], m[PB];
 #pragma unroll
     for (int i = 0; i < PB; ++i)
@@ -529,23 +544,6 @@ __device__ __noinline__ float tc_merge_row(int64_t gr, int cnt, int kth, unsigne
     for (int i = 1; i < PB; ++i)
         kv = (kth >> 5) == i ? m[i] : kv;
     return key_dist(__shfl_sync(0xffffffffu, kv, kth & 31));
-}
-
-// a[j] for a run-time j in [0, 32): a five-level select tree (no local memory)
-__device__ __forceinline__ float pick32(const float (&a)[32], int j)
-{
-    float l1[16], l2[8], l3[4];
-#pragma unroll
-    for (int i = 0; i < 16; ++i)
-        l1[i] = (j & 16) ? a[i + 16] : a[i];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-        l2[i] = (j & 8) ? l1[i + 8] : l1[i];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-        l3[i] = (j & 4) ? l2[i + 4] : l2[i];
-    const float x = (j & 2) ? l3[2] : l3[0], y = (j & 2) ? l3[3] : l3[1];
-    return (j & 1) ? y : x;
 }
 
 // tcgen05.ld of 32 columns without the wait; tmem_wait32 completes it (its
@@ -583,11 +581,24 @@ __device__ __forceinline__ void load_h(float4 (&h)[8], const float4 *__restrict_
         h[i] = __ldg(p + i);
 }
 
-// One 32-column chunk of a row: the running maximum of q.x - |x|^2 / 2 decides
-// whether any column passes; a passing lane builds its hit mask and appends each
-// hit's (distance, id) key to the row's buffer.
-__device__ __forceinline__ void tc_chunk(const uint32_t (&v)[32], const float4 (&hq)[8], float tr, float qnr,
-                                         int64_t cb, int64_t self, unsigned long long *__restrict__ brow, int &cnt)
+// tcgen05.ld of one column (each lane its own TMEM lane) and its wait
+__device__ __forceinline__ uint32_t tmem_ld1(uint32_t taddr)
+{
+    uint32_t x;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n\ttcgen05.wait::ld.sync.aligned;"
+                 : "=r"(x)
+                 : "r"(taddr)
+                 : "memory");
+    return x;
+}
+
+// One 32-column chunk of a row in the split float form: the running maximum of
+// q.x - |x|^2 / 2 decides whether any column passes; then the whole warp visits
+// the passing columns of all its rows once each, reading each back from TMEM
+// (taddr = the chunk's first column; hc = the chunk's half norms).
+__device__ __forceinline__ void tc_chunk(const uint32_t (&v)[32], const float4 (&hq)[8], uint32_t taddr,
+                                         const float *__restrict__ hc, float tr, float qnr, int64_t cb, int64_t self,
+                                         unsigned long long *__restrict__ brow, int &cnt)
 {
     float a[32];
 #pragma unroll
@@ -606,7 +617,7 @@ __device__ __forceinline__ void tc_chunk(const uint32_t (&v)[32], const float4 (
         m2 = fmaxf(m2, a[j + 2]);
         m3 = fmaxf(m3, a[j + 3]);
     }
-    if (!(fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) > tr))
+    if (!__any_sync(0xffffffffu, fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) > tr))
         return;
     unsigned hit = 0;
 #pragma unroll
@@ -615,24 +626,29 @@ __device__ __forceinline__ void tc_chunk(const uint32_t (&v)[32], const float4 (
     const int64_t sj = self - cb;
     if (sj >= 0 && sj < 32)
         hit &= ~(1u << (int)sj);
-    while (hit) {
-        const int j = __ffs(hit) - 1;
-        hit &= hit - 1;
-        brow[cnt++] = pack_key(fmaxf(qnr - 2.f * pick32(a, j), 0.f), (int)(cb + j));
+    unsigned cols = __reduce_or_sync(0xffffffffu, hit);
+    while (cols) {
+        const int j = __ffs(cols) - 1;
+        cols &= cols - 1;
+        const float x = __uint_as_float(tmem_ld1(taddr + (uint32_t)j)) - __ldg(hc + j);
+        if ((hit >> j) & 1u)
+            brow[cnt++] = pack_key(fmaxf(qnr - 2.f * x, 0.f), (int)(cb + j));
     }
 }
 
 // The byte-valued form of a chunk: the accumulator already holds
 // v = q.x - floor(|x|^2 / 2) (the MMA adds the spare K atom's pieces), an integer,
-// and v >= q.x - |x|^2 / 2, so v >= tr selects a superset of the hits; a passing
-// lane corrects each candidate by the parity of |x|^2 (one bit per column in
-// par, loaded only here) to a = q.x - |x|^2 / 2 and keeps it when a >= tr, i.e.
-// d^2 <= thr.  The comparison is not strict because thr is the k-th distance so
-// far here (ranking is exact, so the list needs no slack): a later column at that
-// distance may still win its tie by id.  Columns past n (zero rows of the last
-// tile) are skipped.
-__device__ __forceinline__ void tc_chunk_aug(const uint32_t (&v)[32], float tr, float qnr, int64_t cb, int64_t self,
-                                             int64_t n, const unsigned *__restrict__ par,
+// and v >= q.x - |x|^2 / 2, so v >= tr selects a superset of the hits; a candidate
+// is corrected by the parity of |x|^2 (one bit per column in par, loaded only
+// here) to a = q.x - |x|^2 / 2 and kept when a >= tr, i.e. d^2 <= thr.  The
+// comparison is not strict because thr is the k-th distance so far here (ranking
+// is exact, so the list needs no slack): a later column at that distance may still
+// win its tie by id.  Columns past n (zero rows of the last tile) are skipped.
+// Called by the whole warp: the candidate columns of all 32 rows are visited
+// once each, reading that column back from TMEM (taddr = the chunk's first
+// column), so no lane indexes its registers at run time.
+__device__ __forceinline__ void tc_chunk_aug(const uint32_t (&v)[32], uint32_t taddr, float tr, float qnr, int64_t cb,
+                                             int64_t self, int64_t n, const unsigned *__restrict__ par,
                                              unsigned long long *__restrict__ brow, int &cnt)
 {
     const float *f = reinterpret_cast<const float *>(v);
@@ -646,29 +662,30 @@ __device__ __forceinline__ void tc_chunk_aug(const uint32_t (&v)[32], float tr, 
         for (int i = 0; i < 8; ++i)
             m[i] = fmaxf(m[i], f[j + i]);
     const float mx = fmaxf(fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3])), fmaxf(fmaxf(m[4], m[5]), fmaxf(m[6], m[7])));
-    if (!(mx >= tr))
+    if (!__any_sync(0xffffffffu, mx >= tr))
         return;
-    float a[32];
     unsigned hit = 0;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        a[j] = f[j];
-        hit |= (a[j] >= tr ? 1u : 0u) << j;
-    }
+    for (int j = 0; j < 32; ++j)
+        hit |= (f[j] >= tr ? 1u : 0u) << j;
     const int64_t sj = self - cb;
     if (sj >= 0 && sj < 32)
         hit &= ~(1u << (int)sj);
     if (n - cb < 32)
         hit &= n - cb > 0 ? (1u << (int)(n - cb)) - 1u : 0u;
-    if (!hit)
+    unsigned cols = __reduce_or_sync(0xffffffffu, hit);
+    if (!cols)
         return;
     const unsigned odd = __ldg(par + (cb >> 5));
-    while (hit) {
-        const int j = __ffs(hit) - 1;
-        hit &= hit - 1;
-        const float aj = pick32(a, j) - ((odd >> j) & 1u ? 0.5f : 0.f);
-        if (aj >= tr)
-            brow[cnt++] = pack_key(fmaxf(qnr - 2.f * aj, 0.f), (int)(cb + j));
+    while (cols) {
+        const int j = __ffs(cols) - 1;
+        cols &= cols - 1;
+        const float x = __uint_as_float(tmem_ld1(taddr + (uint32_t)j));
+        if ((hit >> j) & 1u) {
+            const float aj = x - ((odd >> j) & 1u ? 0.5f : 0.f);
+            if (aj >= tr)
+                brow[cnt++] = pack_key(fmaxf(qnr - 2.f * aj, 0.f), (int)(cb + j));
+        }
     }
 }
 
@@ -715,28 +732,34 @@ __device__ void tc_epilogue(uint64_t *accf, uint64_t *acce, uint32_t tmem, int w
         for (int c = 0; c < TC_N / 32; c += 2) {
             tmem_ld32_async(tb + (uint32_t)((c + 1) * 32), vb);
             if constexpr (AUG) {
-                tc_chunk_aug(va, tr, qnr, col0 + c * 32, self, n, par, brow, cnt);
+                tc_chunk_aug(va, tb + (uint32_t)(c * 32), tr, qnr, col0 + c * 32, self, n, par, brow, cnt);
             } else {
                 load_h(hq, h4 + c * 8);
-                tc_chunk(va, hq, tr, qnr, col0 + c * 32, self, brow, cnt);
+                tc_chunk(va, hq, tb + (uint32_t)(c * 32), xh + col0 + c * 32, tr, qnr, col0 + c * 32, self, brow,
+                         cnt);
             }
             tmem_wait32(vb);
             if (c + 2 < TC_N / 32)
                 tmem_ld32_async(tb + (uint32_t)((c + 2) * 32), va);
             if constexpr (AUG) {
-                tc_chunk_aug(vb, tr, qnr, col0 + (c + 1) * 32, self, n, par, brow, cnt);
+                tc_chunk_aug(vb, tb + (uint32_t)((c + 1) * 32), tr, qnr, col0 + (c + 1) * 32, self, n, par, brow,
+                             cnt);
             } else {
                 load_h(hq, h4 + (c + 1) * 8);
-                tc_chunk(vb, hq, tr, qnr, col0 + (c + 1) * 32, self, brow, cnt);
+                tc_chunk(vb, hq, tb + (uint32_t)((c + 1) * 32), xh + col0 + (c + 1) * 32, tr, qnr,
+                         col0 + (c + 1) * 32, self, brow, cnt);
             }
             if (c + 2 < TC_N / 32)
                 tmem_wait32(va);
         }
         tc_fence_before();
         mbar_arrive(&acce[b]);
-        // rows whose buffer may not absorb another tile (or all, after the last)
+        // rows whose buffer may not absorb another tile, or holds TC_EAGER keys (an
+        // earlier merge lowers the threshold, which saves later appends: cheaper
+        // than the smaller sorts it costs), and all rows after the last tile
         const bool last = t + 1 == tiles;
-        unsigned need = __ballot_sync(0xffffffffu, row_ok && (cnt > TC_BUF - TC_N || (last && cnt > 0)));
+        unsigned need = __ballot_sync(0xffffffffu, row_ok && (cnt > TC_BUF - TC_N || cnt >= TC_EAGER ||
+                                                              (last && cnt > 0)));
         while (need) {
             const int src = __ffs(need) - 1;
             need &= need - 1;
