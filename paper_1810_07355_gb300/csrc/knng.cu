@@ -208,13 +208,14 @@ __global__ void __launch_bounds__(NT, 2)
     }
 }
 
-// Rescores the KC survivors of each row by direct difference and writes the best k.
-template <int KC>
+// Rescores the survivors of each row by direct difference and writes the best k:
+// NL lists of KC keys per row (list l of row r at best[l * lstride + r * KC]).
+template <int KC, int NL = 1>
 __global__ void knn_final_kernel(const float *__restrict__ X, int d, const float *__restrict__ Q, int64_t nq,
                                  const unsigned long long *__restrict__ best, int k, int32_t *__restrict__ nbr,
-                                 float *__restrict__ len)
+                                 float *__restrict__ len, int64_t lstride = 0)
 {
-    constexpr int PER = KC / 32;
+    constexpr int PER = KC * NL / 32;
     const int lane = threadIdx.x & 31;
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (row >= nq)
@@ -223,7 +224,8 @@ __global__ void knn_final_kernel(const float *__restrict__ X, int d, const float
     const float4 *q4 = reinterpret_cast<const float4 *>(Q + row * d);
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
-        const unsigned long long key = best[row * KC + i * 32 + lane];
+        const int e = i * 32 + lane;
+        const unsigned long long key = best[(int64_t)(e / KC) * lstride + row * KC + e % KC];
         const int id = key_id(key);
         // every lane walks the 32 candidates of this slice in turn
         float mine = INFINITY;
@@ -689,6 +691,19 @@ __device__ __forceinline__ void tc_chunk_aug(const uint32_t (&v)[32], uint32_t t
     }
 }
 
+// Which base tiles a CTA sweeps, in order: its u-th tile is (t0 + g + u G) mod
+// `all`, for u < count.  G CTAs share a row set and take every G-th tile (g = this
+// CTA's share); t0 rotates a self-join's sweep to start at its own rows.
+struct TileMap {
+    int64_t all, t0, count;
+    int G, g;
+    __device__ TileMap(int64_t all_, int64_t t0_, int G_, int g_)
+        : all(all_), t0(t0_), count((all_ - g_ + G_ - 1) / G_), G(G_), g(g_)
+    {
+    }
+    __device__ __forceinline__ int64_t tile(int64_t u) const { return (t0 + g + u * G) % all; }
+};
+
 // The epilogue of the tensor-core kernels (warps 0-7; see knn_tc_kernel): one
 // query row per thread, tile by tile from the TMEM accumulators (row block rb =
 // warp / 4 at columns (2 rb + b) * TC_N, b = tile & 1).
@@ -696,7 +711,7 @@ __device__ __forceinline__ void tc_chunk_aug(const uint32_t (&v)[32], uint32_t t
 // the split float form (tc_chunk with the padded half norms `xh`).
 template <int KC, bool AUG>
 __device__ void tc_epilogue(uint64_t *accf, uint64_t *acce, uint32_t tmem, int warp, int lane, int64_t row0,
-                            int64_t nq, int64_t n, int64_t tiles, int64_t t0, int kth, int64_t self_offset,
+                            int64_t nq, int64_t n, const TileMap tm, int kth, int64_t self_offset,
                             const float *__restrict__ xh,
                             const unsigned *__restrict__ par, const float *__restrict__ qn,
                             unsigned long long *__restrict__ best, unsigned long long *__restrict__ buf, int *err)
@@ -710,13 +725,13 @@ __device__ void tc_epilogue(uint64_t *accf, uint64_t *acce, uint32_t tmem, int w
     int cnt = 0;
     unsigned long long *brow = buf + (row_ok ? grow : 0) * TC_BUF;
     const uint32_t lane_base = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(rb * 2 * TC_N);
-    for (int64_t t = 0; t < tiles; ++t) {
+    for (int64_t t = 0; t < tm.count; ++t) {
         const int b = (int)(t & 1);
         const bool ok = mbar_wait(&accf[b], (uint32_t)((t >> 1) & 1), err, 5);
         if (!__all_sync(0xffffffffu, ok))
             break;
         tc_fence_after();
-        const int64_t col0 = ((t + t0) % tiles) * TC_N;
+        const int64_t col0 = tm.tile(t) * TC_N;
         // d^2 = |q|^2 + |x|^2 - 2 q.x < thr  <=>  q.x - |x|^2 / 2 > (|q|^2 - thr) / 2, every
         // term an exact integer or half-integer for byte-valued inputs (approximate in
         // the split float form, whose survivors are rescored)
@@ -757,7 +772,7 @@ __device__ void tc_epilogue(uint64_t *accf, uint64_t *acce, uint32_t tmem, int w
         // rows whose buffer may not absorb another tile, or holds TC_EAGER keys (an
         // earlier merge lowers the threshold, which saves later appends: cheaper
         // than the smaller sorts it costs), and all rows after the last tile
-        const bool last = t + 1 == tiles;
+        const bool last = t + 1 == tm.count;
         unsigned need = __ballot_sync(0xffffffffu, row_ok && (cnt > TC_BUF - TC_N || cnt >= TC_EAGER ||
                                                               (last && cnt > 0)));
         while (need) {
@@ -891,7 +906,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else {
         // ------------------------------------------------ epilogue (warps 0-7)
-        tc_epilogue<KC, true>(accf, acce, tmem, warp, lane, row0, nq, n, tiles, t0, k - 1, self_offset, nullptr, par, qn,
+        tc_epilogue<KC, true>(accf, acce, tmem, warp, lane, row0, nq, n, TileMap(tiles, t0, 1, 0), k - 1, self_offset, nullptr, par, qn,
                               best, buf, err);
     }
     tc_fence_before();
@@ -927,7 +942,7 @@ template <int KC>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     knn_tcs_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                    const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int64_t n,
-                   int64_t nq, int nk, int64_t self_offset, const float *__restrict__ xh,
+                   int64_t nq, int nk, int G, int64_t self_offset, const float *__restrict__ xh,
                    const float *__restrict__ qn, unsigned long long *__restrict__ best,
                    unsigned long long *__restrict__ buf, int *err)
 {
@@ -939,13 +954,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acce + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t row0 = (int64_t)blockIdx.x * TC_ROWS;
+    const int64_t row0 = (int64_t)(blockIdx.x / G) * TC_ROWS;
     const int64_t tiles = (n + TC_N - 1) / TC_N;
-    const int64_t steps = tiles * nk;
     const int nrb = row0 + TC_M < nq ? TC_RB : 1;  // row blocks holding any query row
     // a self-join starts its sweep at the tile of its own rows and wraps around:
     // where nearby rows sit together, the thresholds fall within the first tiles
     const int64_t t0 = self_offset >= 0 ? ((self_offset + row0) / TC_N) % tiles : 0;
+    const TileMap tm(tiles, t0, G, (int)(blockIdx.x % G));
+    const int64_t steps = tm.count * nk;
+    // this CTA's lists: share g of the row set keeps its own best list and buffers
+    best += (int64_t)tm.g * nq * KC;
+    buf += (int64_t)tm.g * nq * TC_BUF;
 
     if (tid == 0) {
         for (int s = 0; s < TCS_STAGES; ++s) {
@@ -991,8 +1010,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tma_load_2d(st + rb * L::ATOM, &tmAh, kc * 64, (int)(row0 + rb * TC_M), &full[s]);
                     tma_load_2d(st + (2 + rb) * L::ATOM, &tmAl, kc * 64, (int)(row0 + rb * TC_M), &full[s]);
                 }
-                tma_load_2d(st + 4 * L::ATOM, &tmBh, kc * 64, (int)(((t + t0) % tiles) * TC_N), &full[s]);
-                tma_load_2d(st + 5 * L::ATOM, &tmBl, kc * 64, (int)(((t + t0) % tiles) * TC_N), &full[s]);
+                tma_load_2d(st + 4 * L::ATOM, &tmBh, kc * 64, (int)(tm.tile(t) * TC_N), &full[s]);
+                tma_load_2d(st + 5 * L::ATOM, &tmBl, kc * 64, (int)(tm.tile(t) * TC_N), &full[s]);
                 issued = step + 1;
             }
             // our copies in flight complete before the CTA may exit (bounded)
@@ -1042,7 +1061,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else {
         // ------------------------------------------------ epilogue (warps 0-7)
-        tc_epilogue<KC, false>(accf, acce, tmem, warp, lane, row0, nq, n, tiles, t0, KC - 1, self_offset, xh, nullptr, qn,
+        tc_epilogue<KC, false>(accf, acce, tmem, warp, lane, row0, nq, n, tm, KC - 1, self_offset, xh, nullptr, qn,
                                best, buf, err);
     }
     tc_fence_before();
@@ -1196,6 +1215,12 @@ int make_map(CUtensorMap *m, const void *ptr, int64_t rows, int d, int box_rows)
     return ONNG_OK;
 }
 
+// CTAs sharing one row set in the split sweep: above d = 128 a CTA's A chunks
+// (256 rows x dp x 4 bytes) over all resident CTAs would exceed L2, so two CTAs take
+// alternate tiles of the same rows (half the A data in flight) and keep a best list
+// each, merged by the rescore.
+int split_share(int d) { return d > 128 ? 2 : 1; }
+
 int pick_kc(int k)
 {
     for (int kc = 32; kc <= 256; kc <<= 1)
@@ -1276,15 +1301,15 @@ int launch_tc(const float *X, int64_t n, int d, const float *Q, int64_t nq, int 
 }
 
 template <int KC>
-int launch_tcs_kc(const CUtensorMap *m, int64_t n, int64_t nq, int nk, int64_t self_offset, const float *xh,
+int launch_tcs_kc(const CUtensorMap *m, int64_t n, int64_t nq, int nk, int G, int64_t self_offset, const float *xh,
                   const float *qn, unsigned long long *best, unsigned long long *bufp, int *err, cudaStream_t s)
 {
     const size_t smem = TcsSmem::BYTES;
     ONNG_CUDA_TRY(cudaFuncSetAttribute(reinterpret_cast<const void *>(knn_tcs_kernel<KC>),
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                   "onng_knn: split tensor kernel smem attribute");
-    knn_tcs_kernel<KC><<<(unsigned)((nq + TC_ROWS - 1) / TC_ROWS), TC_THREADS, smem, s>>>(
-        m[0], m[1], m[2], m[3], n, nq, nk, self_offset, xh, qn, best, bufp, err);
+    knn_tcs_kernel<KC><<<(unsigned)((nq + TC_ROWS - 1) / TC_ROWS * G), TC_THREADS, smem, s>>>(
+        m[0], m[1], m[2], m[3], n, nq, nk, G, self_offset, xh, qn, best, bufp, err);
     return check_launch("onng_knn: split tensor kernel");
 }
 
@@ -1311,9 +1336,10 @@ int launch_tcs(const float *X, int64_t n, int d, const float *Q, int64_t nq, int
         (st = make_map(&m[2], xhi, n, dp, TC_N)) || (st = make_map(&m[3], xlo, n, dp, TC_N)))
         return st;
     const int nk = dp / 64;
-    st = kc == 32 ? launch_tcs_kc<32>(m, n, nq, nk, self_offset, xh, qn, best, bufp, err, s)
-         : kc == 64 ? launch_tcs_kc<64>(m, n, nq, nk, self_offset, xh, qn, best, bufp, err, s)
-                    : launch_tcs_kc<128>(m, n, nq, nk, self_offset, xh, qn, best, bufp, err, s);
+    const int G = split_share(d);
+    st = kc == 32 ? launch_tcs_kc<32>(m, n, nq, nk, G, self_offset, xh, qn, best, bufp, err, s)
+         : kc == 64 ? launch_tcs_kc<64>(m, n, nq, nk, G, self_offset, xh, qn, best, bufp, err, s)
+                    : launch_tcs_kc<128>(m, n, nq, nk, G, self_offset, xh, qn, best, bufp, err, s);
     if (st)
         return st;
     int code = 0;
@@ -1322,12 +1348,22 @@ int launch_tcs(const float *X, int64_t n, int d, const float *Q, int64_t nq, int
     if (code)
         return set_error(ONNG_E_LIMIT, "onng_knn: tensor-core pipeline wait timed out (role %d)", code);
     const unsigned grid = (unsigned)((nq * 32 + 255) / 256);
-    if (kc == 32)
-        knn_final_kernel<32><<<grid, 256, 0, s>>>(X, d, Q, nq, best, k, nbr, len);
-    else if (kc == 64)
-        knn_final_kernel<64><<<grid, 256, 0, s>>>(X, d, Q, nq, best, k, nbr, len);
-    else
-        knn_final_kernel<128><<<grid, 256, 0, s>>>(X, d, Q, nq, best, k, nbr, len);
+    const int64_t ls = nq * kc;  // the G lists of a row
+    if (G == 1) {
+        if (kc == 32)
+            knn_final_kernel<32><<<grid, 256, 0, s>>>(X, d, Q, nq, best, k, nbr, len);
+        else if (kc == 64)
+            knn_final_kernel<64><<<grid, 256, 0, s>>>(X, d, Q, nq, best, k, nbr, len);
+        else
+            knn_final_kernel<128><<<grid, 256, 0, s>>>(X, d, Q, nq, best, k, nbr, len);
+    } else {
+        if (kc == 32)
+            knn_final_kernel<32, 2><<<grid, 256, 0, s>>>(X, d, Q, nq, best, k, nbr, len, ls);
+        else if (kc == 64)
+            knn_final_kernel<64, 2><<<grid, 256, 0, s>>>(X, d, Q, nq, best, k, nbr, len, ls);
+        else
+            knn_final_kernel<128, 2><<<grid, 256, 0, s>>>(X, d, Q, nq, best, k, nbr, len, ls);
+    }
     return check_launch("onng_knn: final kernel");
 }
 
@@ -1342,8 +1378,8 @@ extern "C" size_t onng_knn_workspace_bytes(int64_t n, int32_t d, int64_t nq, int
     WsCarver c(nullptr);
     c.take<float>((size_t)std::max<int64_t>(n, 1));
     c.take<float>((size_t)std::max<int64_t>(nq, 1));
-    c.take<unsigned long long>((size_t)std::max<int64_t>(nq, 1) * (kc ? kc : 32));
-    c.take<unsigned long long>((size_t)std::max<int64_t>(nq, 1) * std::max(BUF, TC_BUF));
+    c.take<unsigned long long>((size_t)std::max<int64_t>(nq, 1) * (kc ? kc : 32) * split_share(d));
+    c.take<unsigned long long>((size_t)std::max<int64_t>(nq, 1) * std::max(BUF, TC_BUF) * split_share(d));
     c.take<int>(64);
     // bfloat16 copies: hi and lo rows of dp = 64 ceil(d / 64) (the byte path's rows of d + 64 fit)
     const size_t dp = (size_t)(std::max(d, 1) + 63) / 64 * 64;
@@ -1375,8 +1411,8 @@ extern "C" int onng_knn(const float *X, int64_t n, int32_t d, const float *Q, in
     WsCarver c(ws);
     float *xn = c.take<float>((size_t)std::max<int64_t>(n, 1));
     float *qn = c.take<float>((size_t)nq);
-    unsigned long long *best = c.take<unsigned long long>((size_t)nq * kc);
-    unsigned long long *bufp = c.take<unsigned long long>((size_t)nq * std::max(BUF, TC_BUF));
+    unsigned long long *best = c.take<unsigned long long>((size_t)nq * kc * split_share(d));
+    unsigned long long *bufp = c.take<unsigned long long>((size_t)nq * std::max(BUF, TC_BUF) * split_share(d));
     int *flags = c.take<int>(64);
     const size_t dp = (size_t)(d + 63) / 64 * 64;
     __nv_bfloat16 *xb = c.take<__nv_bfloat16>((size_t)std::max<int64_t>(n, 1) * dp * 2);
