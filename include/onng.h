@@ -338,6 +338,46 @@ int onng_search_noalloc(const onng_index *idx, const float *Q, int64_t nq, const
 int onng_pad_adjacency(const int64_t *row_ptr, const int32_t *col, int64_t n, int32_t width,
                        int32_t *adj, onng_stream_t stream);
 
+/* --------------------------------------------------------------------- serving
+ * A search service with continuous batching (the serving pattern of a request
+ * stream over a device-resident index; no paper counterpart).  Requests of 1 ..
+ * max_queries query vectors (host memory, copied at submit), each with its own k,
+ * eps and e_s, are batched by one worker thread: a launch takes the (k, eps, e_s)
+ * class of the oldest pending request and, in arrival order, every pending request
+ * of that class that fits, copies their queries to the device, runs
+ * onng_seeds_pivot (n_pivot, n_seed) and onng_search (precision, k_rerank) on its
+ * own stream and copies the results back; up to `slots` launches are in flight.
+ * A request's result depends only on its queries and class, never on its batch.
+ *   onng_serve_create:  starts the service over `idx` (its arrays stay owned by
+ *                       the caller and must outlive the server) on the current
+ *                       device; allocates the slots' device and pinned host
+ *                       buffers (the one part of the library that allocates).
+ *   onng_serve_submit:  queues Q [nq, d] (host) and returns a ticket; thread-safe.
+ *   onng_serve_poll:    waits up to timeout_ms for the ticket's results and copies
+ *                       ids [nq, k] and dist [nq, k] (host memory); ONNG_E_LIMIT if
+ *                       not done yet (poll again); the ticket is consumed once
+ *                       the results (or a failure) are returned.
+ *   onng_serve_destroy: stops the worker, waits for launches in flight and frees
+ *                       every buffer; tickets not polled are dropped.
+ * A launch still running after timeout_ms (the watchdog) fails its requests with
+ * ONNG_E_LIMIT and stops the server: later submits and polls of pending requests
+ * return that status.  A failed launch does the same with its own status. */
+typedef struct onng_server onng_server;
+typedef struct {
+    int32_t precision;        /* ONNG_PREC_* of every launch */
+    int32_t k_rerank;         /* reduced precision: candidates rescored in float32 (max with k) */
+    int32_t n_pivot, n_seed;  /* the pivot seed rule of onng_seeds_pivot */
+    int32_t max_queries;      /* queries per launch (and at most per request) */
+    int32_t k_max;            /* the largest k a request may ask */
+    int32_t slots;            /* launches in flight, one stream each (1 .. 64) */
+    int32_t timeout_ms;       /* watchdog per launch */
+} onng_serve_config;
+int onng_serve_create(const onng_index *idx, const onng_serve_config *cfg, onng_server **out);
+int onng_serve_submit(onng_server *srv, const float *Q, int32_t nq, int32_t k, float eps, int32_t e_s,
+                      uint64_t *ticket);
+int onng_serve_poll(onng_server *srv, uint64_t ticket, int32_t *ids, float *dist, int32_t timeout_ms);
+int onng_serve_destroy(onng_server *srv);
+
 /* ------------------------------------------------------- parameter predictor
  * A 16 -> 64 -> 64 -> 2 network with ReLU hidden layers mapping probe features
  * to (log(eps + 0.01), log e_s) per query (no paper counterpart; it replaces the

@@ -42,6 +42,11 @@ class _GraphStats(C.Structure):
                 ("bottom5_in", C.c_double), ("in_dist10", C.c_double)]
 
 
+class _ServeConfig(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("k_rerank", C.c_int32), ("n_pivot", C.c_int32), ("n_seed", C.c_int32),
+                ("max_queries", C.c_int32), ("k_max", C.c_int32), ("slots", C.c_int32), ("timeout_ms", C.c_int32)]
+
+
 class _Params(C.Structure):
     _fields_ = [("k", C.c_int32), ("e_s", C.c_int32), ("eps", C.c_float), ("precision", C.c_int32),
                 ("k_rerank", C.c_int32), ("max_expansions", C.c_int32), ("pool_cap", C.c_int32)]
@@ -109,6 +114,10 @@ def load(build_if_missing: bool = True):
             "onng_index_check": ([C.c_char_p, vp, vp, vp, vp], C.c_int),
             "onng_index_load": ([C.c_char_p, i64, i32, i64, vp, vp, vp, vp, vp], C.c_int),
             "onng_crc32": ([C.c_uint32, vp, sz], C.c_uint32),
+            "onng_serve_create": ([C.POINTER(_Index), C.POINTER(_ServeConfig), C.POINTER(vp)], C.c_int),
+            "onng_serve_submit": ([vp, vp, i32, i32, f32, i32, C.POINTER(C.c_uint64)], C.c_int),
+            "onng_serve_poll": ([vp, C.c_uint64, vp, vp, i32], C.c_int),
+            "onng_serve_destroy": ([vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -130,7 +139,8 @@ def exported_symbols():
         "onng_adjust_degree_sac_workspace_bytes", "onng_adjust_degree_sac_count", "onng_adjust_degree_sac",
         "onng_adjust_path_literal_workspace_bytes", "onng_adjust_path_literal",
         "onng_graph_stats_workspace_bytes", "onng_graph_stats", "onng_index_save", "onng_index_check",
-        "onng_index_load", "onng_crc32",
+        "onng_index_load", "onng_crc32", "onng_serve_create", "onng_serve_submit", "onng_serve_poll",
+        "onng_serve_destroy",
     ]
 
 
@@ -576,3 +586,55 @@ def mlp_predict(P, X, alpha: float = 1.0, es_min: int = 1, es_max: int = 32):
     _check(load().onng_mlp_predict(_ptr(_dev(P, torch.float32)), _ptr(X), B, float(alpha), es_min, es_max, _ptr(eps),
                                    _ptr(es), _stream()))
     return eps, es
+
+
+# ----------------------------------------------------------------------------- serving service
+
+class Service:
+    """The library's own serving loop (onng_serve_*): a native worker thread batches
+    submitted requests by (k, eps, e_s) class over `slots` CUDA streams.  Queries
+    are host float32 arrays; results come back as host arrays."""
+
+    def __init__(self, index: "Index", precision: int = PREC_FP32, k_rerank: int = 0, n_pivot: int = 1024,
+                 n_seed: int = 10, max_queries: int = 1024, k_max: int = 100, slots: int = 4,
+                 timeout_ms: int = 10000):
+        self.index = index  # its tensors must outlive the service
+        self._ix = index._c()
+        cfg = _ServeConfig(precision, k_rerank, n_pivot, n_seed, max_queries, k_max, slots, timeout_ms)
+        self._h = C.c_void_p()
+        self._shape = {}
+        _check(load().onng_serve_create(C.byref(self._ix), C.byref(cfg), C.byref(self._h)))
+
+    def submit(self, Q, k: int, eps: float, e_s: int) -> int:
+        import numpy as np
+        Q = np.ascontiguousarray(Q, dtype=np.float32)
+        t = C.c_uint64(0)
+        _check(load().onng_serve_submit(self._h, Q.ctypes.data_as(C.c_void_p), Q.shape[0], k, eps, e_s,
+                                        C.byref(t)))
+        self._shape[t.value] = (Q.shape[0], k)
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = 10000):
+        """(ids, dist) as numpy arrays [nq, k], or None if not done within timeout_ms."""
+        import numpy as np
+        nq, k = self._shape[ticket]
+        ids = np.empty((nq, k), np.int32)
+        dist = np.empty((nq, k), np.float32)
+        st = load().onng_serve_poll(self._h, ticket, ids.ctypes.data_as(C.c_void_p),
+                                    dist.ctypes.data_as(C.c_void_p), timeout_ms)
+        if st == ONNG_E_LIMIT and b"not done yet" in load().onng_last_error():
+            return None
+        del self._shape[ticket]
+        _check(st)
+        return ids, dist
+
+    def close(self):
+        if self._h:
+            load().onng_serve_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

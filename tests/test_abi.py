@@ -153,3 +153,16 @@ def test_index_file_check(lib, tmp_path):
     _write_index_file(good, rp, col, ln, X)
     st = lib.onng_index_load(str(good).encode(), 4, 8, 5, C.c_void_p(8), C.c_void_p(8), None, C.c_void_p(8), None)
     assert st == onng.ONNG_E_INVAL and b"expects" in lib.onng_last_error()
+
+
+def test_serve_argument_checks(lib):
+    from paper_1810_07355_gb300 import onng
+    out = C.c_void_p()
+    cfg = onng._ServeConfig(0, 0, 256, 10, 64, 10, 2, 1000)
+    st = lib.onng_serve_create(None, C.byref(cfg), C.byref(out))
+    assert st == onng.ONNG_E_INVAL and out.value is None
+    ix = onng._Index(None, None, C.c_void_p(16), None, None, 100, 128, 0)
+    for bad in (onng._ServeConfig(0, 0, 256, 10, 64, 10, 0, 1000), onng._ServeConfig(0, 0, 256, 10, 0, 10, 2, 1000),
+                onng._ServeConfig(0, 0, 256, 10, 64, 10, 2, 0)):
+        assert lib.onng_serve_create(C.byref(ix), C.byref(bad), C.byref(out)) == onng.ONNG_E_INVAL
+    assert lib.onng_serve_destroy(None) == onng.ONNG_OK
