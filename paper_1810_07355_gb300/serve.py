@@ -357,6 +357,53 @@ def calibrate_eps(index, Q, k_values, recalls, e_s_options, n_pivot, n_seed, pre
     return table
 
 
+def run_native(index, table: dict, trace, Q: np.ndarray, precision: int, k_rerank: int, slots: int,
+               n_pivot: int = 1024, timeout_ms: int = 10_000) -> ServeResult:
+    """The same trace through the library's native service (onng_serve_*): a host
+    thread submits each request at its arrival time with its class's (eps, e_s);
+    this thread polls the tickets in arrival order and takes the moment a poll
+    returns as the request's completion (so a request that finished before an
+    earlier one was collected counts the wait)."""
+    import threading
+    n = len(trace)
+    out = ServeResult(ids=[None] * n, dist=[None] * n, latency={}, launches=0, wall=0.0)
+    tickets = [None] * n
+    ready = threading.Condition()
+    import sys
+    switch = sys.getswitchinterval()
+    sys.setswitchinterval(2e-4)  # the two host threads hand over the interpreter often
+    with onng.Service(index, precision=precision, k_rerank=k_rerank, n_pivot=n_pivot, max_queries=4096,
+                      k_max=100, slots=slots, timeout_ms=timeout_ms) as svc:
+        t0 = time.perf_counter()
+
+        def submitter():
+            for rid in range(n):
+                r = trace[rid]
+                delay = float(r["arrival"]) - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+                eps, es = table[(int(r["k"]), float(r["recall"]))]
+                t = svc.submit(Q[r["first"]:r["first"] + r["size"]], int(r["k"]), float(eps), int(es))
+                with ready:
+                    tickets[rid] = t
+                    ready.notify()
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        for rid in range(n):
+            with ready:
+                ready.wait_for(lambda: tickets[rid] is not None)
+            res = None
+            while res is None:
+                res = svc.poll(tickets[rid], timeout_ms)
+            out.latency[rid] = time.perf_counter() - t0 - trace["arrival"][rid]
+            out.ids[rid], out.dist[rid] = res
+        th.join()
+        out.wall = time.perf_counter() - t0
+    sys.setswitchinterval(switch)
+    return out
+
+
 def serve_spec(seconds: float = 60.0, rate: float = 100_000.0, precisions=("fp8", "bf16"), slots: int = 4,
                ws_mb: int = 1024, e_s: int = 10, k_rerank: int = 32, capacity_rate: float = 0.0,
                timeout_s: float = 10.0) -> dict:
@@ -401,6 +448,18 @@ def serve_spec(seconds: float = 60.0, rate: float = 100_000.0, precisions=("fp8"
             ids, dist = srv.search_alone(Q[r["first"]:r["first"] + r["size"]], int(r["k"]), float(r["recall"]))
             ok += int(np.array_equal(ids, res.ids[rid]) and np.array_equal(dist, res.dist[rid]))
         same[key] = f"{ok}/{len(sample)}"
+        if name == "bf16":
+            # the same trace through the native service (worker thread in the library)
+            run_native(index, table, trace[: min(len(trace), 200)], Q, prec, kr, slots)  # warm-up
+            nat = run_native(index, table, trace, Q, prec, kr, slots)
+            nsum = nat.summary(trace)
+            nsum.pop("launches", None)
+            nsum.pop("workspace_peak_bytes", None)
+            nsum.pop("workspace_waits", None)
+            ok_n = sum(int(np.array_equal(nat.ids[rid], res.ids[rid]) and np.array_equal(nat.dist[rid], res.dist[rid]))
+                       for rid in sample)
+            runs["bf16_native_service"] = dict(nsum, precision=name, k_rerank=kr, slots=slots,
+                                               same_as_python_loop=f"{ok_n}/{len(sample)}")
         if capacity_rate > 0 and name != "fp32":
             ctrace = synth.request_trace(min(seconds, 2.0), capacity_rate, seed=synth.SEED_BASE + 6)
             _, CQ = synth.workload("gmm10k", nq=int(ctrace["size"].sum()))
