@@ -437,17 +437,38 @@ __global__ void path_big_kernel(const int64_t *__restrict__ rp, const int32_t *_
             if (!(liu < lmax))
                 continue;
             const int m = col[beg + u];
-            const int64_t mb = rp[m], me = rp[m + 1];
-            for (int64_t idx = mb + lane; idx < me; idx += 32) {
-                const float lmj = len[idx];
-                if (!(lmj < lmax))
-                    break;
-                const int t = ghash_find(hkey, hpos, cap, col[idx]);
-                if (t < 0)
-                    continue;
-                const float lij = len[beg + t];
-                if (liu < lij && lmj < lij)
-                    atomicMin(&wit[beg + t], u);
+            const int64_t mb = rp[m];
+            // the prefix of m's list shorter than lmax (rows are sorted by length)
+            int64_t lo = 0, hi = rp[m + 1] - mb;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (len[mb + mid] < lmax)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            const int64_t me = mb + lo;
+            // kPathUnroll entries per lane in flight
+            for (int64_t i0 = mb + lane; i0 < me; i0 += 32 * kPathUnroll) {
+                float lmj[kPathUnroll];
+                int cj[kPathUnroll];
+#pragma unroll
+                for (int r = 0; r < kPathUnroll; ++r) {
+                    const int64_t idx = i0 + 32 * r;
+                    lmj[r] = idx < me ? len[idx] : INFINITY;
+                    cj[r] = idx < me ? col[idx] : -1;
+                }
+#pragma unroll
+                for (int r = 0; r < kPathUnroll; ++r) {
+                    if (cj[r] < 0)
+                        continue;
+                    const int t = ghash_find(hkey, hpos, cap, cj[r]);
+                    if (t < 0)
+                        continue;
+                    const float lij = len[beg + t];
+                    if (liu < lij && lmj[r] < lij)
+                        atomicMin(&wit[beg + t], u);
+                }
             }
         }
         __syncthreads();

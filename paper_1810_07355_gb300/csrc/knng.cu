@@ -269,6 +269,22 @@ __global__ void knn_final_kernel(const float *__restrict__ X, int d, const float
     }
 }
 
+// The byte-valued tensor-core form ranks exactly: its best lists are already in
+// (squared distance, id) order with the exact integer squared distances a float32
+// direct-difference rescore would recompute, so the first k entries are written
+// as they are.
+__global__ void knn_emit_kernel(int64_t nq, const unsigned long long *__restrict__ best, int kc, int k,
+                                int32_t *__restrict__ nbr, float *__restrict__ len)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nq * k; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = e / k;
+        const unsigned long long key = best[row * kc + e % k];
+        const int id = key_id(key);
+        nbr[e] = id;
+        len[e] = id < 0 ? INFINITY : sqrtf(key_dist(key));
+    }
+}
+
 // ---------------------------------------------------------------- tensor cores
 //
 // knn_tc_kernel: the same sweep with the dot products on the 5th-generation
@@ -1287,17 +1303,8 @@ int launch_tc(const float *X, int64_t n, int d, const float *Q, int64_t nq, int 
     ONNG_CUDA_TRY(cudaStreamSynchronize(s), "onng_knn: tensor kernel");
     if (code)
         return set_error(ONNG_E_LIMIT, "onng_knn: tensor-core pipeline wait timed out (role %d)", code);
-    switch (kc) {
-    case 32:
-        knn_final_kernel<32><<<(unsigned)((nq * 32 + 255) / 256), 256, 0, s>>>(X, d, Q, nq, best, k, nbr, len);
-        break;
-    case 64:
-        knn_final_kernel<64><<<(unsigned)((nq * 32 + 255) / 256), 256, 0, s>>>(X, d, Q, nq, best, k, nbr, len);
-        break;
-    default:
-        knn_final_kernel<128><<<(unsigned)((nq * 32 + 255) / 256), 256, 0, s>>>(X, d, Q, nq, best, k, nbr, len);
-    }
-    return check_launch("onng_knn: final kernel");
+    knn_emit_kernel<<<gb, 256, 0, s>>>(nq, best, kc, k, nbr, len);
+    return check_launch("onng_knn: output");
 }
 
 template <int KC>
