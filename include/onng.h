@@ -61,14 +61,14 @@ int onng_version(void);
  * ordered by (length, id).  If self_offset >= 0, query row r is base point
  * self_offset + r and that id is excluded (a duplicate point with another id is
  * still a neighbour).  k <= 256.  Rows with fewer than k candidates are padded
- * with -1 / +inf.  A sweep over the base ranks the expanded form |q|^2 + |x|^2 -
- * 2 q.x and keeps KC >= k + 16 survivors per row, which are rescored by direct
- * difference in float32: byte-valued inputs (integers 0-255) at d = 64 / 128 on
- * the tensor cores, exactly; other non-integer inputs at d >= 32 on the tensor
- * cores with both sets centred on the base mean and split into bfloat16 hi + lo
- * (dot products to about 2^-16 |q| |x|); the rest by a float32 SIMT sweep
- * (integer-valued inputs with squared norms below 2^23 exactly).  Inputs must be
- * finite.
+ * with -1 / +inf.  Three sweeps over the base: byte-valued inputs (integers
+ * 0-255) at d = 64 / 128 on the tensor cores, ranked exactly (the lists are
+ * written as ranked); other non-integer inputs at d >= 32 on the tensor cores
+ * with both sets centred on the base mean and split into bfloat16 hi + lo (dot
+ * products to about 2^-16 |q| |x|), and the rest by a float32 SIMT sweep
+ * (integer-valued inputs with squared norms below 2^23 exactly); these two rank
+ * the expanded form |q|^2 + |x|^2 - 2 q.x, keep KC >= k + 16 survivors per row and
+ * rescore them by direct difference in float32.  Inputs must be finite.
  *
  * onng_build_knng(X, n, d, k, ...) == onng_knn(X, n, d, X, n, k, 0, ...).
  */
