@@ -63,8 +63,9 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 NAMES = {"fp32": "plain fp32", "bf16": "fixed-eps bf16 + fp32 rerank", "fp8": "fixed-eps fp8 e4m3 + fp32 rerank",
          "eq1": "Eq. 1 policy (e_s = 10^(20 eps) + 30), bf16 + fp32 rerank",
+         "bf16cap": "fixed-eps bf16 + fp32 rerank, expansions capped at the p99 of the uncapped run",
          "learned": "learned per-query eps/e_s, bf16 + fp32 rerank"}
-VEC_BYTES = {"fp32": 4, "bf16": 2, "fp8": 1, "eq1": 2, "learned": 2}
+VEC_BYTES = {"fp32": 4, "bf16": 2, "fp8": 1, "eq1": 2, "bf16cap": 2, "learned": 2}
 # Pivots of the seed rule per workload: enough that every cluster of the
 # clustered stand-ins holds several (a cluster without one is reached only
 # through the graph's inter-cluster edges, which the kNN graph of well-separated
@@ -103,7 +104,7 @@ def parse(argv=None):
                          "at each (the learned form re-selects its shrinkage); reported under by_target")
     ap.add_argument("--k-rerank", type=int, default=20)
     ap.add_argument("--probe-hops", type=int, default=4)
-    ap.add_argument("--forms", default="fp32,bf16,fp8,eq1,learned",
+    ap.add_argument("--forms", default="fp32,bf16,fp8,eq1,bf16cap,learned",
                     help="forms to time (comma list of fp32, bf16, fp8, eq1, learned); the value is the last one")
     ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--eps-fp32", type=float, default=None, help="use this eps instead of calibrating")
@@ -408,6 +409,21 @@ def main():
 
     eps16 = a.eps_bf16 if a.eps_bf16 is not None else calibrate(run16, gt, a.target)
     points["bf16"] = {"eps": round(eps16, 5), "e_s": a.e_s}
+    eps16c, cap16 = None, 0
+    if "bf16cap" in forms:
+        # the batch waits for its slowest queries: cap every query's expansions at
+        # the 99th percentile of the uncapped run's counts, then bisect eps again
+        # so that the mean recall still reaches the target
+        st16 = run16(eps16)[2]
+        cap16 = max(1, int(np.percentile(st16[:, 1].cpu().numpy(), 99)))
+
+        def run16c(eps):
+            return onng.search(idx, Qd, a.k, a.e_s, eps, seeds, precision=onng.PREC_BF16, k_rerank=a.k_rerank,
+                               max_expansions=cap16)
+        eps16c = calibrate(run16c, gt, a.target)
+        capped = int((run16c(eps16c)[2][:, 3] & onng.FLAG_LIMIT).ne(0).sum())
+        points["bf16cap"] = {"eps": round(eps16c, 5), "e_s": a.e_s, "max_expansions": cap16,
+                             "queries_capped": capped, "cap_rule": "99th percentile of the uncapped bf16 run"}
     eps8 = None
     if "fp8" in forms:
         eps8 = calibrate(run8, gt, a.target)
@@ -490,6 +506,9 @@ def main():
         elif form == "eq1":
             ids, _, st = onng.search(idx_eq1, Qd, a.k, es_eq1, eps_eq1, s, precision=onng.PREC_BF16,
                                      k_rerank=a.k_rerank)
+        elif form == "bf16cap":
+            ids, _, st = onng.search(idx, Qd, a.k, a.e_s, eps16c, s, precision=onng.PREC_BF16, k_rerank=a.k_rerank,
+                                     max_expansions=cap16)
         else:
             ids, _, st = onng.search(idx, Qd, a.k, a.e_s, eps16, s, precision=onng.PREC_BF16, k_rerank=a.k_rerank)
         return ids, st, e
@@ -537,6 +556,8 @@ def main():
     head = forms[-1]
     if head == "learned" and learned_info["fixed_policy_cheaper_on_select_queries"] and "bf16" in forms:
         head = "bf16"
+    if "bf16cap" in forms and head != "fp32" and qps["bf16cap"] > qps[head]:
+        head = "bf16cap"  # the faster of the bf16 forms at the target recall
     traffic = None
     kform = "fp32" if head == "fp32" else "bf16"
     if os.path.exists(TRAFFIC) and a.workload == "sift1m":
@@ -574,6 +595,8 @@ def main():
         for t in (float(x) for x in a.extra_targets.split(",") if x):
             row = {}
             for f in forms:
+                if f == "bf16cap":
+                    continue  # timed at the main target only
                 if f == "learned":
                     best_t, ybar_t, table_t = learned.select_shrinkage(
                         pred_raw, idx, Qtrd[ntr:], gt_tr[ntr:], seeds_tr[ntr:], a.k, t, t_pred,
@@ -625,7 +648,9 @@ def main():
     sweep = None
     if not a.no_sweep and rank == 0:
         sweep = degree_sweep(onng, torch, a, Xd, Qd, knn_lists, seeds, gt, flush)
-    e2e = end_to_end(onng, torch, a, idx, Q, head, pred, t_pred, alpha, eps32 if head == "fp32" else eps16, dev)
+    e2e = end_to_end(onng, torch, a, idx, Q, head, pred, t_pred, alpha,
+                     eps32 if head == "fp32" else eps16c if head == "bf16cap" else eps16, dev,
+                     cap=cap16 if head == "bf16cap" else 0)
     log("end to end done")
     cpu, parity = None, None
     if rank == 0 and world == 1:
@@ -634,7 +659,7 @@ def main():
         cpu = cpu_baseline(a, idx, X, Q, seeds, eps32, parity=inputs)
         if inputs is not None:
             cpu, parity = cpu["baseline"], cpu["parity"]
-    per_step = {"fp32": 2, "bf16": 2, "fp8": 2, "eq1": 2, "learned": 4}
+    per_step = {"fp32": 2, "bf16": 2, "fp8": 2, "eq1": 2, "bf16cap": 2, "learned": 4}
     if rank == 0:
         line = {"metric": METRIC, "value": round(qps[head], 1), "unit": "queries/s", "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms[head], 4),
@@ -767,7 +792,7 @@ def tune_degrees(onng, torch, a, Xd, Qd, knn_lists, seeds, build, p_l=0.90, p_u=
     print(json.dumps(line), flush=True)
 
 
-def end_to_end(onng, torch, a, idx, Q, form, pred, t_pred, alpha, eps, dev):
+def end_to_end(onng, torch, a, idx, Q, form, pred, t_pred, alpha, eps, dev, cap=0):
     """The timed form through the public API with host buffers: H2D of the
     queries, then seeds, (probe, predictor,) search, and D2H of ids and distances."""
     pin_q = torch.from_numpy(Q).pin_memory()
@@ -783,9 +808,9 @@ def end_to_end(onng, torch, a, idx, Q, form, pred, t_pred, alpha, eps, dev):
             eq, es = onng.mlp_predict(pred.P, feat, alpha, pred.es_min, pred.es_max)
             ids, dist, _ = onng.search(idx, q, a.k, pred.es_max, 0.0, s, precision=onng.PREC_BF16,
                                        k_rerank=a.k_rerank, eps_q=eq, es_q=es, stats=False)
-        elif form == "bf16":
+        elif form in ("bf16", "bf16cap"):
             ids, dist, _ = onng.search(idx, q, a.k, a.e_s, eps, s, precision=onng.PREC_BF16, k_rerank=a.k_rerank,
-                                       stats=False)
+                                       max_expansions=cap, stats=False)
         else:
             ids, dist, _ = onng.search(idx, q, a.k, a.e_s, eps, s, stats=False)
         out_ids.copy_(ids, non_blocking=True)
