@@ -67,6 +67,9 @@ def _load():
             lib.oracle_search.argtypes = [vp, vp, vp, i64, i32, vp, i64, i32, i32, dbl, vp, i32,
                                           vp, vp, vp, i32]
             lib.oracle_search.restype = i32
+            lib.oracle_search_capped.argtypes = [vp, vp, vp, i64, i32, vp, i64, i32, i32, dbl, vp, i32, i64,
+                                                 vp, vp, vp, i32]
+            lib.oracle_search_capped.restype = i32
             lib.oracle_search_margin.argtypes = [vp, vp, vp, i64, i32, vp, i64, i32, i32, dbl, vp, i32,
                                                  vp, vp, vp, vp, i32]
             lib.oracle_search_margin.restype = i32
@@ -239,7 +242,8 @@ def hash_selftest(ids, n: int):
     return out.astype(bool)
 
 
-def search(ptr, col, X, Q, k: int, e_s: int, eps: float, seeds, threads: int = 0, margin: bool = False):
+def search(ptr, col, X, Q, k: int, e_s: int, eps: float, seeds, threads: int = 0, margin: bool = False,
+           max_exp: int = 0):
     """Algorithm 1 for every query.  Returns (ids int32, dist float64, stats int64 [nq,4]).
 
     With ``margin`` also returns, per query, the smallest relative gap of any
@@ -263,6 +267,11 @@ def search(ptr, col, X, Q, k: int, e_s: int, eps: float, seeds, threads: int = 0
                                           threads)
         assert rc == 0, rc
         return ids, dist, stats, mg
+    if max_exp > 0:
+        rc = _load().oracle_search_capped(_p(ptr), _p(col), _p(X), n, d, _p(Q), nq, k, e_s, float(eps),
+                                          _p(seeds), seeds.shape[1], max_exp, _p(ids), _p(dist), _p(stats), threads)
+        assert rc == 0, rc
+        return ids, dist, stats
     rc = _load().oracle_search(_p(ptr), _p(col), _p(X), n, d, _p(Q), nq, k, e_s, float(eps),
                                _p(seeds), seeds.shape[1], _p(ids), _p(dist), _p(stats), threads)
     assert rc == 0, rc

@@ -21,6 +21,7 @@
  *   oracle_adjust_path_alg4  Algorithm 4 taken literally (round-robin, ascending ids)
  *   oracle_search         KnnSearch, Algorithm 1, with the visited set of
  *                         Algorithms Set/IsSet (Sec. 2.5) and e_p of Eq. 1 as e_s
+ *   oracle_search_capped  the same search with at most max_exp expansions per query
  *   oracle_search_margin  the same search, also returning per query the smallest
  *                         relative gap of any comparison it decided (a test aid:
  *                         how close the run came to a tie)
@@ -938,7 +939,7 @@ static int search_core(const int64_t *ptr, const int32_t *col, const float *X, i
                 stats[qi * 4 + 0] = ndc;
                 stats[qi * 4 + 1] = nexp;
                 stats[qi * 4 + 2] = maxs;
-                stats[qi * 4 + 3] = 0;
+                stats[qi * 4 + 3] = capped ? 4 : 0; /* stopped by max_exp with an in-bound candidate left */
             }
             if (feat) {
                 /* features of the probe, in the order of the library's probe output */
@@ -988,6 +989,19 @@ int oracle_search(const int64_t *ptr, const int32_t *col, const float *X, int64_
 {
     return search_core(ptr, col, X, n, d, Q, nq, k, e_s, eps, seeds, n_seed, out_ids, out_dist,
                        stats, threads, 0, 0.0, NULL, NULL);
+}
+
+/* Algorithm 1 with at most max_exp expansions per query (0: no cap): a run that
+ * reaches the cap stops before popping again; stats[q*4+3] = 4 when it stopped
+ * with an in-bound candidate left (an operating-point parameter of the batched
+ * search, not part of the paper's Algorithm 1). */
+int oracle_search_capped(const int64_t *ptr, const int32_t *col, const float *X, int64_t n, int d,
+                         const float *Q, int64_t nq, int k, int e_s, double eps, const int32_t *seeds,
+                         int n_seed, int64_t max_exp, int32_t *out_ids, double *out_dist, int64_t *stats,
+                         int threads)
+{
+    return search_core(ptr, col, X, n, d, Q, nq, k, e_s, eps, seeds, n_seed, out_ids, out_dist,
+                       stats, threads, max_exp, 0.0, NULL, NULL);
 }
 
 int oracle_search_margin(const int64_t *ptr, const int32_t *col, const float *X, int64_t n, int d,

@@ -322,6 +322,25 @@ def test_search_integer_exact(onng, sift_graph, k, e_s, eps, padded):
     assert (host(st)[:, 3] == 0).all()
 
 
+@pytest.mark.parametrize("cap,prec", [(1, 0), (9, 0), (60, 0), (60, 1)])
+def test_search_expansion_cap_integer_exact(onng, sift_graph, cap, prec):
+    """A per-query expansion cap (the bench's capped form): the ids, distance
+    computations, expansions and the LIMIT flag equal the capped oracle's; bf16 is
+    exact on these byte-valued vectors, so its reranked lists match too."""
+    X, Q, g, seeds = sift_graph
+    idx = onng.Index(g[0], g[1], dev(X)).with_adjacency(20).with_bf16()
+    kw = dict(precision=onng.PREC_BF16, k_rerank=10) if prec else {}
+    ids, dist, st = onng.search(idx, dev(Q), 10, 20, 0.12, seeds, max_expansions=cap, **kw)
+    o_ids, o_dist, o_st = oracle.search(host(g[0]), host(g[1]), X, Q, 10, 20, np.float32(0.12), host(seeds),
+                                        max_exp=cap)
+    assert np.array_equal(host(ids), o_ids)
+    np.testing.assert_allclose(host(dist), o_dist, rtol=1e-6)
+    assert np.array_equal(host(st)[:, 0], o_st[:, 0])
+    assert np.array_equal(host(st)[:, 1], o_st[:, 1])
+    assert np.array_equal(host(st)[:, 3] & onng.FLAG_LIMIT, o_st[:, 3])
+    assert (host(st)[:, 1] <= cap).all()
+
+
 def test_search_unbounded_is_exact_knn(onng, sift_graph):
     """eps = inf with every edge scanned visits every node of a strongly
     connected graph, so the search returns the exact k nearest neighbours."""

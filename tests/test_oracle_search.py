@@ -334,3 +334,32 @@ def test_fp8_quantize_scales_and_error_bound(oracle_lib):
     # the column maximum is stored exactly (it scales to 448, a code)
     j = np.abs(X).argmax(0)
     assert np.allclose(np.abs(xq[j, np.arange(24)]), mx, rtol=1e-6)
+
+
+def test_expansion_cap(oracle_lib, one_cluster):
+    """The capped search: a cap no query reaches changes nothing; with a cap of one
+    expansion and eps = inf the result is the k nearest of the seeds and the first
+    e_s neighbours of the nearest seed (brute force), flagged 4 when a candidate
+    was left; expansion counts never exceed the cap."""
+    X, Q, (ptr, col, _) = one_cluster
+    n = len(X)
+    seeds = oracle_lib.seeds_random(11, len(Q), n, 3)
+    ids, dist, st = oracle_lib.search(ptr, col, X, Q, 10, 6, 0.1, seeds)
+    c_ids, c_dist, c_st = oracle_lib.search(ptr, col, X, Q, 10, 6, 0.1, seeds, max_exp=int(st[:, 1].max()) + 1)
+    assert np.array_equal(ids, c_ids) and np.array_equal(st[:, :2], c_st[:, :2]) and (c_st[:, 3] == 0).all()
+    c_ids, c_dist, c_st = oracle_lib.search(ptr, col, X, Q, 10, 6, np.inf, seeds, max_exp=1)
+    assert (c_st[:, 1] == 1).all()
+    X64, Q64 = X.astype(np.float64), Q.astype(np.float64)
+    for q in range(len(Q)):
+        sd = np.sqrt(((X64[seeds[q]] - Q64[q]) ** 2).sum(1))
+        first = seeds[q][np.lexsort((seeds[q], sd))[0]]
+        cand = np.unique(np.concatenate([seeds[q], col[ptr[first]:ptr[first] + 6]]))
+        cd = np.sqrt(((X64[cand] - Q64[q]) ** 2).sum(1))
+        order = np.lexsort((cand, cd))[:10]
+        want = np.full(10, -1)
+        want[:len(order)] = cand[order]
+        assert np.array_equal(c_ids[q], want), q
+        assert c_st[q, 3] == (4 if len(cand) > 1 else 0)
+    for cap in (2, 5):
+        _, _, c_st = oracle_lib.search(ptr, col, X, Q, 10, 6, 0.1, seeds, max_exp=cap)
+        assert (c_st[:, 1] <= cap).all()
