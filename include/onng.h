@@ -320,12 +320,11 @@ int onng_search_probe(const onng_index *idx, const float *Q, int64_t nq, const o
  * are fine: they run on as many CTAs as the array holds (26 at n = 1M), each
  * taking queries until none are left.
  *
- * The first call on a device looks up the array's device address (with that
- * device current) and keeps it; make that first call before any stream
- * capture.  The kept address belongs to the device's primary context: after
- * cudaDeviceReset (or anything else that tears that context down) do not call
- * this entry point again in the same process.  Every call clears the parts that must start at zero (the query
- * counter and the bitmaps) on its stream, so a call sees nothing of the
+ * Every call looks up the array's device address with the caller's device
+ * current, so the entry point stays valid after cudaDeviceReset; make the
+ * first call on a device before any stream capture, since that lookup may
+ * load the module.  Every call clears the parts that must start at zero (the
+ * query counter and the bitmaps) on its stream, so a call sees nothing of the
  * previous one.  All calls on a device share the one array: calls whose
  * kernels can overlap on the GPU (other streams, other host threads) race
  * and give wrong results; order them on one stream or with events. */

@@ -3,7 +3,6 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
-#include <mutex>
 
 #include "search_kernel.cuh"
 
@@ -241,30 +240,19 @@ extern "C" int onng_search_probe(const onng_index *idx, const float *Q, int64_t 
 //
 // Host code must not hand `g_noalloc_scratch` to a kernel: here that name is a
 // host-side stand-in for the symbol, not its device address.  The address is
-// looked up once per device, with that device current, and then reused.
+// looked up on every call, with the caller's device current, so a device reset
+// or a reloaded module never leaves a stale pointer behind.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[ONNG_SEARCH_NOALLOC_SCRATCH_BYTES];
 
 namespace onng {
 namespace {
 
-constexpr int kNoallocMaxDevices = 64;
-
 int noalloc_scratch(void **out)
 {
-    static std::mutex mu;
-    static void *addr[kNoallocMaxDevices] = {};
-    int dev = -1;
-    ONNG_CUDA_TRY(cudaGetDevice(&dev), "onng_search_noalloc: current device");
-    ONNG_REQUIRE(dev >= 0 && dev < kNoallocMaxDevices, ONNG_E_UNSUPPORTED,
-                 "onng_search_noalloc: device ordinal %d >= %d", dev, kNoallocMaxDevices);
-    std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
-        void *ptr = nullptr;
-        ONNG_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_noalloc_scratch), "onng_search_noalloc: scratch address");
-        ONNG_REQUIRE(ptr, ONNG_E_CUDA, "onng_search_noalloc: scratch address is NULL");
-        addr[dev] = ptr;
-    }
-    *out = addr[dev];
+    void *ptr = nullptr;
+    ONNG_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_noalloc_scratch), "onng_search_noalloc: scratch address");
+    ONNG_REQUIRE(ptr, ONNG_E_CUDA, "onng_search_noalloc: scratch address is NULL");
+    *out = ptr;
     return ONNG_OK;
 }
 
