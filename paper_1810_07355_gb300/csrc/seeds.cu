@@ -60,16 +60,21 @@ __global__ void seeds_random_kernel(unsigned long long global_seed, int64_t nq, 
 // tiles of kPivT: each tile (in chunks of kPivD coordinates) and the CTA's
 // queries are staged in shared memory, and thread (i, j) accumulates the
 // squared distances of query i to pivots j, j + 16, j + 32, j + 48 of the tile
-// by direct difference in float32.  After each tile a warp per query merges the
-// tile's 64 (distance, pivot index) keys into the query's sorted list of its 64
-// best so far (a bitonic sort of 128 keys, skipped when no key of the tile beats
-// the list's n_seed-th).  Every pivot row is read once per CTA instead of once
-// per query, and shared memory does not grow with the pivot count.
+// by direct difference in float32, coordinate by coordinate.  After each tile a
+// warp per query folds the tile's 64 (distance, pivot index) keys into the
+// query's sorted list of its 64 best so far.  Only keys below the list's
+// n_seed-th take part: a few of them are inserted one at a time; when many
+// qualify (the first tiles) the list and the tile are bitonic-sorted together.
+// Every pivot row is read once per CTA instead of once per query, and shared
+// memory (33 KB, so that five CTAs share an SM) does not grow with the pivot
+// count.
 constexpr int kPivQ = 16;
 constexpr int kPivT = 64;
-constexpr int kPivD = 128;
+constexpr int kPivD = 64;
 constexpr int kPivThreads = 256;
+constexpr int kPivMinCta = 5;
 constexpr int kPivRow = kPivD + 4;  // padded tile row: conflict-free 16-byte reads
+constexpr int kPivInsertMax = 16;   // at most this many qualifying keys: insert one by one
 constexpr unsigned long long kNoKey = ~0ull;
 
 size_t pivot_smem_bytes()
@@ -78,7 +83,20 @@ size_t pivot_smem_bytes()
            sizeof(unsigned long long) * (size_t)kPivQ * kMaxSeed;
 }
 
-__global__ void __launch_bounds__(kPivThreads)
+// Inserts `key` (warp-uniform, absent from the list) into the ascending list
+// whose element e = h * 32 + lane is b[h] of lane `lane`; the last element drops.
+__device__ __forceinline__ void list_insert(unsigned long long (&b)[2], unsigned long long key, int lane)
+{
+    const int pos = __popc(__ballot_sync(0xffffffffu, b[0] < key)) + __popc(__ballot_sync(0xffffffffu, b[1] < key));
+    const unsigned long long up0 = __shfl_up_sync(0xffffffffu, b[0], 1);
+    const unsigned long long up1 = __shfl_up_sync(0xffffffffu, b[1], 1);
+    const unsigned long long last0 = __shfl_sync(0xffffffffu, b[0], 31);
+    const int e1 = 32 + lane;
+    b[0] = lane < pos ? b[0] : (lane == pos ? key : up0);
+    b[1] = e1 < pos ? b[1] : (e1 == pos ? key : (lane == 0 ? last0 : up1));
+}
+
+__global__ void __launch_bounds__(kPivThreads, kPivMinCta)
     seeds_pivot_kernel(const float *__restrict__ X, int64_t n, int d, const float *__restrict__ Q, int64_t nq, int P,
                        int n_seed, int32_t *__restrict__ out)
 {
@@ -139,24 +157,48 @@ __global__ void __launch_bounds__(kPivThreads)
         for (int mm = 0; mm < 4; ++mm)
             dist[qi * kPivT + pj + 16 * mm] = acc[mm];
         __syncthreads();
-        // merge the tile into each query's best list: keys (distance bits, pivot
+        // fold the tile into each query's best list: keys (distance bits, pivot
         // index) order as (distance, index) for non-negative distances; NaN
         // distances (non-finite input) are never taken
         for (int i = warp; i < kPivQ; i += kPivThreads / 32) {
-            unsigned long long v[4];
             unsigned long long *bl = best + i * kMaxSeed;
+            unsigned long long b[2], v[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int t = t0 + lane + 32 * h;
                 const float dv = dist[i * kPivT + lane + 32 * h];
-                v[2 + h] = (t < P && !isnan(dv)) ? pack_key(dv, t) : kNoKey;
-                v[h] = bl[lane + 32 * h];
+                v[h] = (t < P && !isnan(dv)) ? pack_key(dv, t) : kNoKey;
+                b[h] = bl[lane + 32 * h];
             }
-            const unsigned long long kth = bl[m - 1];
-            if (__any_sync(0xffffffffu, v[2] < kth || v[3] < kth)) {
-                warp_bitonic_sort<4>(v, lane);
-                bl[lane] = v[0];
-                bl[32 + lane] = v[1];
+            const bool hi = m > 32;  // the n_seed-th key sits in b[1]
+            unsigned long long kth = __shfl_sync(0xffffffffu, hi ? b[1] : b[0], (m - 1) & 31);
+            unsigned in0 = __ballot_sync(0xffffffffu, v[0] < kth);
+            unsigned in1 = __ballot_sync(0xffffffffu, v[1] < kth);
+            const int cnt = __popc(in0) + __popc(in1);
+            if (cnt > kPivInsertMax) {
+                unsigned long long s[4] = {b[0], b[1], v[0], v[1]};
+                warp_bitonic_sort<4>(s, lane);
+                b[0] = s[0];
+                b[1] = s[1];
+            } else {
+                while (in0 | in1) {
+                    const bool first = in0 != 0;
+                    const unsigned mk = first ? in0 : in1;
+                    const int src = __ffs(mk) - 1;
+                    if (first)
+                        in0 &= in0 - 1;
+                    else
+                        in1 &= in1 - 1;
+                    const unsigned long long key = __shfl_sync(0xffffffffu, first ? v[0] : v[1], src);
+                    if (key < kth) {
+                        list_insert(b, key, lane);
+                        kth = __shfl_sync(0xffffffffu, hi ? b[1] : b[0], (m - 1) & 31);
+                    }
+                }
+            }
+            if (cnt) {
+                bl[lane] = b[0];
+                bl[32 + lane] = b[1];
             }
             __syncwarp();
         }
@@ -172,7 +214,6 @@ __global__ void __launch_bounds__(kPivThreads)
         }
     }
 }
-
 }  // namespace
 }  // namespace onng
 
