@@ -354,25 +354,28 @@ __device__ void path_row_warp(int64_t i, const int64_t *__restrict__ rp, const i
     __syncwarp();
 }
 
+// Warps stride over the rows (the grid is what stays resident), so a warp whose
+// row ends early takes the next one instead of idling until the slowest row of
+// its CTA is done.
 __global__ void __launch_bounds__(kPathWarps * 32)
     path_small_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const float *__restrict__ len,
                       int64_t n, int *__restrict__ wit, int64_t *__restrict__ big_rows, int *__restrict__ n_big)
 {
     __shared__ PathSmem sm[kPathWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * kPathWarps + warp;
-    if (i >= n)
-        return;
-    const int64_t deg = rp[i + 1] - rp[i];
-    if (deg > kPathSmall) {
-        if (lane == 0)
-            big_rows[atomicAdd(n_big, 1)] = i;
-        return;
+    const int64_t stride = (int64_t)gridDim.x * kPathWarps;
+    for (int64_t i = (int64_t)blockIdx.x * kPathWarps + warp; i < n; i += stride) {
+        const int64_t deg = rp[i + 1] - rp[i];
+        if (deg > kPathSmall) {
+            if (lane == 0)
+                big_rows[atomicAdd(n_big, 1)] = i;
+            continue;
+        }
+        if (deg >= 2)
+            path_row_warp(i, rp, col, len, sm[warp], wit, lane);
+        else if (deg == 1 && lane == 0)
+            wit[rp[i]] = -1;
     }
-    if (deg >= 2)
-        path_row_warp(i, rp, col, len, sm[warp], wit, lane);
-    else if (deg == 1 && lane == 0)
-        wit[rp[i]] = -1;
 }
 
 // Open-addressing table of any size `cap` (range reduction by multiply-high).
@@ -1112,8 +1115,12 @@ extern "C" int onng_adjust_path(const int64_t *row_ptr, const int32_t *col, cons
     int st;
     if (n > 0) {
         ONNG_CUDA_TRY(cudaMemsetAsync(n_big, 0, sizeof(int), s), "adjust_path: clear");
-        path_small_kernel<<<(unsigned)((n + kPathWarps - 1) / kPathWarps), kPathWarps * 32, 0, s>>>(
-            row_ptr, col, len, n, wit, big, n_big);
+        int per_sm = 0;
+        ONNG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, path_small_kernel, kPathWarps * 32, 0),
+                      "adjust_path: occupancy");
+        const int64_t resident = (int64_t)num_sms() * std::max(per_sm, 1);
+        const int64_t ctas = std::min<int64_t>((n + kPathWarps - 1) / kPathWarps, resident);
+        path_small_kernel<<<(unsigned)ctas, kPathWarps * 32, 0, s>>>(row_ptr, col, len, n, wit, big, n_big);
         // hub rows: the kernel reads the count of listed rows on the device
         path_big_kernel<<<num_sms() * 2, 512, 0, s>>>(row_ptr, col, len, wit, big, n_big, skey, spos);
         st = check_launch("onng_adjust_path: mark");
