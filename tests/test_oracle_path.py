@@ -145,3 +145,45 @@ def test_alg4_literal_keeps_superset(oracle_lib, degree_graph):
     P = np.array([[0, 0], [1, 0.3], [2, 0]], np.float64)
     g = _graph_from_edges(P, [(0, 2), (0, 1), (1, 2)])
     assert _edges(*oracle_lib.adjust_path_alg4(*g)[:2]) == {(0, 1), (1, 2)}
+
+
+def _alg4_case(order):
+    """Points A = (0, 0), B = (5, 1), C = (10, 0), D = (5, 2) with edges A->B, A->C,
+    B->D, B->C: |AB| = |BC| = sqrt(26) < |AC| = 10 and |BD| = 1 < |BC|, so the order-free
+    rule drops A->C (witness B).  `order` gives the node ids of A, B, C, D."""
+    pts = {"A": (0, 0), "B": (5, 1), "C": (10, 0), "D": (5, 2)}
+    ids = dict(zip("ABCD", order))
+    P = np.zeros((4, 2), np.float64)
+    for k, v in pts.items():
+        P[ids[k]] = v
+    edges = [(ids[a], ids[b]) for a, b in ("AB", "AC", "BD", "BC")]
+    return ids, _graph_from_edges(P, edges)
+
+
+def test_alg4_literal_rounds_and_ascending_ids_by_hand(oracle_lib):
+    """Algorithm 4 taken literally (rounds; inside a round, nodes by ascending id).
+    Round 1 adds A->B and B->D.  In round 2, A tests A->C against the partial graph:
+    B->C is there only if B came before A in that round.  Traced by hand:
+    B before A drops A->C; A before B keeps it, while the order-free rule drops it in
+    both cases."""
+    for order, drop in (((1, 0, 2, 3), True), ((0, 1, 2, 3), False)):
+        ids, g = _alg4_case(order)
+        a, b, c, d = (ids[k] for k in "ABCD")
+        full = {(a, b), (a, c), (b, d), (b, c)}
+        assert _edges(*oracle_lib.adjust_path(*g)[:2]) == full - {(a, c)}
+        assert _edges(*oracle_lib.adjust_path_alg4(*g)[:2]) == (full - {(a, c)} if drop else full)
+
+
+def test_alg4_literal_witness_added_too_late_by_hand(oracle_lib):
+    """The witness edge 2->1 is node 2's third edge (after 2->3 and 2->4), so it enters
+    the partial graph in round 3, after node 0 has kept 0->1 in round 2; the
+    order-free rule drops 0->1 (|02| = |21| = sqrt(26) < |01| = 10)."""
+    P = np.array([[0, 0], [10, 0], [5, 1], [5, 2], [5, 3.5]], np.float64)
+    g = _graph_from_edges(P, [(0, 2), (0, 1), (2, 3), (2, 4), (2, 1)])
+    full = {(0, 2), (0, 1), (2, 3), (2, 4), (2, 1)}
+    assert _edges(*oracle_lib.adjust_path(*g)[:2]) == full - {(0, 1)}
+    assert _edges(*oracle_lib.adjust_path_alg4(*g)[:2]) == full
+    # lists come out in the order edges were added: ascending length per node
+    ptr, col, ln = oracle_lib.adjust_path_alg4(*g)[:3]
+    assert col[ptr[2]:ptr[3]].tolist() == [3, 4, 1]
+    assert np.allclose(ln[ptr[0]:ptr[1]], [np.sqrt(26.0), 10.0])

@@ -190,6 +190,21 @@ def test_splitmix64_published_vectors(oracle_lib):
         assert oracle_lib.splitmix64(v["state"], len(v["outputs"])) == [int(x, 0) for x in v["outputs"]]
 
 
+def test_random_seeds_from_published_draws(oracle_lib):
+    """The random rule maps the published SplitMix64 outputs z to floor(z * n / 2^64)
+    and redraws repeats; query q starts at state global_seed + q * 2^32."""
+    g = json.load(open(os.path.join(GOLDEN, "splitmix64.json")))
+    z0 = [int(x, 0) for x in g["vectors"][0]["outputs"]]  # state 0
+    z1 = [int(x, 0) for x in g["vectors"][1]["outputs"]]  # state 1234567
+    assert oracle_lib.seeds_random(0, 1, 1000, 3)[0].tolist() == [(z * 1000) >> 64 for z in z0]
+    # query 1 of global seed 1234567 - 2^32 starts at state 1234567
+    gs = (1234567 - (1 << 32)) % (1 << 64)
+    assert oracle_lib.seeds_random(gs, 2, 10**6, 5)[1].tolist() == [(z * 10**6) >> 64 for z in z1]
+    # n = 8: the published draws map to 2, 1, 4, 1, 7; the repeated 1 is redrawn
+    assert [(z * 8) >> 64 for z in z1] == [2, 1, 4, 1, 7]
+    assert oracle_lib.seeds_random(1234567, 1, 8, 4)[0].tolist() == [2, 1, 4, 7]
+
+
 def test_random_seeds_properties(oracle_lib):
     s = oracle_lib.seeds_random(123, 4000, 1000, 10)
     assert s.min() >= 0 and s.max() < 1000
