@@ -17,6 +17,8 @@ ground truth is >= 0.95:
   fp8      the same with FP8 e4m3 vectors (per-dimension scales) and the rerank
   eq1      bf16 + rerank under the paper's fixed policy (Eq. 1): e_s tied to eps
            as e_p = floor(10^(20 eps)) + 30, eps bisected
+  bf16cap  bf16 + rerank with every query's expansions capped at the 99th
+           percentile of the uncapped bf16 run's counts, eps bisected again
   learned  bf16 search with per-query (eps, e_s) from the predictor network:
            probe (first h hops) -> bfloat16 network -> search.  The network is
            trained on the GPU on labels of 15,000 training queries; on 5,000
@@ -24,8 +26,8 @@ ground truth is >= 0.95:
            predicted or fixed) with the fewest distance computations at the
            target; its eps scale alpha is then calibrated like the fixed eps
 `value` is the learned+bf16 form, or the fixed-eps bf16 form when one global eps
-was cheaper than every network setting on the selection queries (both are
-reported).  The vectors (512 MB) exceed the 129 MB L2, and L2 is also flushed
+was cheaper than every network setting on the selection queries, or the capped
+bf16 form when that is faster still (all are reported).  The vectors (512 MB) exceed the 129 MB L2, and L2 is also flushed
 between timed steps.
 
 Outside the timed region the line also carries: build times with their
