@@ -15,15 +15,17 @@ Labels come from sweeps of the plain search over an (eps, e_s) grid.  On
 integer-valued data the plain GPU search equals Algorithm 1 run in float64 bit
 for bit (tested), so these labels are the ones the CPU oracle gives; a test
 checks that on a subset.  Two label forms are provided:
-  - per-query targets: the cheapest cell whose recall@k reaches t.  Per-query
-    recall@10 takes only the values 0, 0.1, ..., 1, so t = 0.95 and 0.99 both
-    mean 10 of 10;
-  - cost-aware (used by default): for a price lambda on a distance computation,
-    the cell maximising recall_q - lambda * cost_q.  Over a query set this is
-    the allocation with the fewest distance computations for its mean recall,
-    so a mean recall such as 0.95 is reached by calibrating lambda alone; easy
-    queries then stop early and hopeless ones are not chased.  Feature 0 of the
-    network input is log10(lambda).
+  - per-query targets (what the benchmark trains on, t in {0.9, 1.0}): the
+    cheapest cell whose recall@k reaches t.  Per-query recall@10 takes only the
+    values 0, 0.1, ..., 1, so t = 0.95 and 0.99 both mean 10 of 10.  Feature 0
+    of the network input is t; a mean recall such as 0.95 is then reached by
+    calibrating the eps scale alpha (calibrate_alpha);
+  - cost-aware (train's default when no targets are given): for a price lambda
+    on a distance computation, the cell maximising recall_q - lambda * cost_q.
+    Over a query set this is the allocation with the fewest distance
+    computations for its mean recall, so a mean recall is reached by
+    calibrating lambda alone (calibrate_lambda); easy queries then stop early
+    and hopeless ones are not chased.  Feature 0 is log10(lambda).
 Everything here except the three kernels is preparation (labels, calibration),
 not the search path.
 """

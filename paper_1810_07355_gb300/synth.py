@@ -108,16 +108,6 @@ def small_integers(n: int, d: int, high: int = 8, seed: int = 7) -> np.ndarray:
     return _rng(seed).integers(0, high, size=(n, d)).astype(np.float32)
 
 
-def random_seeds(nq: int, n: int, n_seed: int, seed: int = 99) -> np.ndarray:
-    """Explicit seed lists: ``n_seed`` distinct node ids per query, uniform, int32."""
-    rng = _rng(seed)
-    m = min(n_seed, n)
-    out = np.empty((nq, m), dtype=np.int32)
-    for q in range(nq):
-        out[q] = rng.choice(n, size=m, replace=False)
-    return out
-
-
 # Named workloads.  Base and query sets share centres (centers_seed) but draw
 # points from different streams (seed + 100 for queries, + 200 for training).
 WORKLOADS = {
