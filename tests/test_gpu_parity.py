@@ -216,6 +216,25 @@ def test_path_hub_rows(onng):
     assert np.array_equal(host(p[3]), o[3])
 
 
+def test_path_hub_row_beyond_shared_memory(onng):
+    """A hub of about 8,000 edges: points on a sphere around one centre point all
+    list the centre first, so its row is far beyond the warp kernel's 256 edges
+    and takes the CTA kernel (its hash in global scratch)."""
+    n, d = 8000, 64
+    rng = np.random.default_rng(12)
+    U = rng.normal(size=(n, d))
+    U /= np.linalg.norm(U, axis=1, keepdims=True)
+    X = np.rint(128.0 + 60.0 * U).clip(0, 255).astype(np.float32)
+    X[0] = 128.0
+    nbr, ln = onng.build_knng(dev(X), 40)
+    g = onng.adjust_degree(nbr, ln, 10, 40)
+    assert np.diff(host(g[0])).max() > 6144
+    p = onng.adjust_path(*g, witnesses=True)
+    o = oracle.adjust_path(host(g[0]), host(g[1]), host(g[2]).astype(np.float64), witnesses=True)
+    _csr_equal(p[:3], o[:3])
+    assert np.array_equal(host(p[3]), o[3])
+
+
 @pytest.mark.parametrize("e_o,e_i", [(10, 30), (20, 20), (5, 13)])
 def test_path_literal_alg4_stepwise(onng, sift_knng, e_o, e_i):
     """Algorithm 4 taken literally on the GPU equals the oracle's round-robin pass
