@@ -166,3 +166,47 @@ def test_serve_argument_checks(lib):
                 onng._ServeConfig(0, 0, 256, 10, 64, 10, 2, 0)):
         assert lib.onng_serve_create(C.byref(ix), C.byref(bad), C.byref(out)) == onng.ONNG_E_INVAL
     assert lib.onng_serve_destroy(None) == onng.ONNG_OK
+
+
+def test_header_is_plain_c_and_a_c_program_links(lib, tmp_path):
+    """include/onng.h compiles as C99 (warnings as errors, -pedantic) and a C
+    program linked against libonng.so calls it with no Python in the process: the
+    version, the index-file CRC-32 (check value 0xCBF43926 on "123456789") and an
+    argument error reported through onng_last_error before any device work."""
+    import shutil
+    import subprocess
+    from paper_1810_07355_gb300 import build
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <string.h>
+#include "onng.h"
+
+int main(void)
+{
+    int st;
+    if (onng_version() < 1)
+        return 1;
+    if (onng_crc32(0u, "123456789", 9) != 0xCBF43926u)
+        return 2;
+    st = onng_knn(NULL, 10, 6, NULL, 10, 5, -1, NULL, NULL, NULL, 0, NULL);
+    if (st != ONNG_E_UNSUPPORTED || strstr(onng_last_error(), "multiple of 4") == NULL)
+        return 3;
+    st = onng_seeds_random(1u, 4, 0, 4, NULL, NULL);
+    if (st != ONNG_E_INVAL)
+        return 4;
+    printf("c abi ok %d\n", onng_version());
+    return 0;
+}
+""")
+    libdir = os.path.dirname(build.LIB)
+    exe = str(tmp_path / "abi")
+    cmd = [gcc, "-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+           str(src), "-o", exe, "-L", libdir, "-lonng", "-Wl,-rpath," + libdir]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and r.stdout.startswith("c abi ok"), (r.returncode, r.stdout, r.stderr)
