@@ -37,8 +37,9 @@ enum onng_status {
     ONNG_E_INVAL = 1,       /* bad argument (negative size, k > n - 1, NULL pointer ...) */
     ONNG_E_WORKSPACE = 2,   /* ws_bytes smaller than the *_workspace_bytes query */
     ONNG_E_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
-    ONNG_E_LIMIT = 4,       /* an iteration cap was reached */
-    ONNG_E_UNSUPPORTED = 5  /* shape outside what the kernels handle (d % 4, k > 128 ...) */
+    ONNG_E_LIMIT = 4,       /* an iteration cap or a time limit was reached */
+    ONNG_E_UNSUPPORTED = 5, /* shape outside what the kernels handle (d % 4, k > 128 ...) */
+    ONNG_E_AGAIN = 6        /* onng_serve_poll: not done within timeout_ms (poll again) */
 };
 
 /* per-query flags, stats[q*4 + 3] */
@@ -353,7 +354,7 @@ int onng_pad_adjacency(const int64_t *row_ptr, const int32_t *col, int64_t n, in
  *                       buffers (the one part of the library that allocates).
  *   onng_serve_submit:  queues Q [nq, d] (host) and returns a ticket; thread-safe.
  *   onng_serve_poll:    waits up to timeout_ms for the ticket's results and copies
- *                       ids [nq, k] and dist [nq, k] (host memory); ONNG_E_LIMIT if
+ *                       ids [nq, k] and dist [nq, k] (host memory); ONNG_E_AGAIN if
  *                       not done yet (poll again); the ticket is consumed once
  *                       the results (or a failure) are returned.
  *   onng_serve_destroy: stops the worker, waits for launches in flight and frees

@@ -336,7 +336,7 @@ extern "C" int onng_serve_poll(onng_server *srv, uint64_t ticket, int32_t *ids, 
     Req *r = it->second;
     if (!srv->cv_done.wait_for(lock, std::chrono::milliseconds(std::max(timeout_ms, 0)),
                                [r] { return r->status >= 0; }))
-        return set_error(ONNG_E_LIMIT, "onng_serve_poll: request %llu not done yet", (unsigned long long)ticket);
+        return set_error(ONNG_E_AGAIN, "onng_serve_poll: request %llu not done yet", (unsigned long long)ticket);
     const int status = r->status;
     if (status == ONNG_OK) {
         std::memcpy(ids, r->ids.data(), sizeof(int32_t) * r->ids.size());

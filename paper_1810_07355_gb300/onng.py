@@ -19,7 +19,7 @@ from . import build as _build
 _lock = threading.Lock()
 _lib = None
 
-ONNG_OK, ONNG_E_INVAL, ONNG_E_WORKSPACE, ONNG_E_CUDA, ONNG_E_LIMIT, ONNG_E_UNSUPPORTED = range(6)
+ONNG_OK, ONNG_E_INVAL, ONNG_E_WORKSPACE, ONNG_E_CUDA, ONNG_E_LIMIT, ONNG_E_UNSUPPORTED, ONNG_E_AGAIN = range(7)
 FLAG_S_OVERFLOW, FLAG_VISIT_OVERFLOW, FLAG_LIMIT, FLAG_CHECK = 1, 2, 4, 8
 PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 
@@ -622,7 +622,7 @@ class Service:
         dist = np.empty((nq, k), np.float32)
         st = load().onng_serve_poll(self._h, ticket, ids.ctypes.data_as(C.c_void_p),
                                     dist.ctypes.data_as(C.c_void_p), timeout_ms)
-        if st == ONNG_E_LIMIT and b"not done yet" in load().onng_last_error():
+        if st == ONNG_E_AGAIN:
             return None
         del self._shape[ticket]
         _check(st)

@@ -210,3 +210,15 @@ int main(void)
     assert r.returncode == 0, r.stderr
     r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0 and r.stdout.startswith("c abi ok"), (r.returncode, r.stdout, r.stderr)
+
+
+def test_status_codes_match_header():
+    """The binding's status constants are the header's enum values."""
+    from paper_1810_07355_gb300 import onng
+    text = open(os.path.join(ROOT, "include", "onng.h")).read()
+    body = re.search(r"enum onng_status \{(.*?)\};", text, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    enum = {m.group(1): int(m.group(2)) for m in re.finditer(r"(ONNG_\w+)\s*=\s*(\d+)", body)}
+    assert len(enum) == 7
+    for name, value in enum.items():
+        assert getattr(onng, name) == value, name
