@@ -222,3 +222,31 @@ def test_status_codes_match_header():
     assert len(enum) == 7
     for name, value in enum.items():
         assert getattr(onng, name) == value, name
+
+
+def test_last_error_is_per_thread(lib):
+    """onng_last_error() is thread-local: two threads that fail differently each
+    read back their own message after both have failed."""
+    import threading
+    from paper_1810_07355_gb300 import onng
+    barrier = threading.Barrier(2)
+    seen = {}
+
+    def knn_fails():
+        st = lib.onng_knn(None, 10, 6, None, 10, 5, -1, None, None, None, 0, None)
+        barrier.wait()
+        seen["knn"] = (st, lib.onng_last_error())
+
+    def seeds_fail():
+        st = lib.onng_seeds_random(1, 4, 100, 0, None, None)
+        barrier.wait()
+        seen["seeds"] = (st, lib.onng_last_error())
+
+    threads = [threading.Thread(target=knn_fails), threading.Thread(target=seeds_fail)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert seen["knn"][0] == onng.ONNG_E_UNSUPPORTED and b"multiple of 4" in seen["knn"][1]
+    assert seen["seeds"][0] == onng.ONNG_E_UNSUPPORTED and b"n_seed" in seen["seeds"][1]
+    assert b"n_seed" not in seen["knn"][1] and b"multiple of 4" not in seen["seeds"][1]
