@@ -38,12 +38,15 @@
 //
 // Path adjustment (Algorithms 4/5, order-free reading): edge (i, j) is dropped
 // if the input graph holds i->m and m->j with len(i,m) < len(i,j) and
-// len(m,j) < len(i,j).  A warp owns a node i: N(i) goes into a shared-memory
-// hash (id -> position); the adjacency lists of all m in N(i) are streamed as
-// one flattened sequence across the lanes, and every hit j that satisfies both
-// strict comparisons records the smallest witness position.  Nodes with more
-// than 256 edges use a CTA and a hash in global scratch.  A count / scan /
-// compact sequence then writes the kept edges in their input order.
+// len(m,j) < len(i,j).  A warp owns a node i at a time (persistent warps stride
+// over the nodes): N(i) goes into a shared-memory hash (id -> position); for
+// every m in N(i) shorter than i's longest edge, the prefix of m's list shorter
+// than that edge (a binary search: rows are sorted by length) is streamed with
+// the others as one flattened sequence across the lanes, and every hit j that
+// satisfies both strict comparisons records the smallest witness position.
+// Nodes with more than 256 edges use a CTA and a hash in global scratch.  A
+// count / scan / compact sequence then writes the kept edges in their input
+// order.
 #include <algorithm>
 #include <cmath>
 #include <vector>
