@@ -117,7 +117,7 @@ def parse(argv=None):
     ap.add_argument("--parity-rows", type=int, default=2000, help="sampled kNN / path rows checked")
     ap.add_argument("--parity-queries", type=int, default=500, help="sampled ground-truth queries checked")
     ap.add_argument("--tune", action="store_true",
-                    help="instead of timing: the degree optimisation of Sec. 4 (Eq. 2 over precision "
+                    help="instead of timing: the degree optimisation of Sec. 2.6 (Eq. 2 over precision "
                          "[0.90, 0.98], hill climb of step 5 from (e_o, e_i)) on this workload")
     ap.add_argument("--tune-queries", type=int, default=2000, help="queries scored by Eq. 2 in --tune")
     ap.add_argument("--build-modes", action="store_true",
@@ -290,7 +290,7 @@ def build_index(onng, torch, Xd, a, peaks):
                          "frac": round(pb / t[2] / 1e9 / hbm, 4), "bytes": int(pb),
                          "note": "input + output CSR + the list of m for every edge (i,m) shorter than i's "
                                  "longest edge, 8 B an entry"}}}
-    # Table 4's statistics of both graphs, and the 1-NNG's indegrees (Sec. 3.1)
+    # Table 4's statistics of both graphs, and the 1-NNG's indegrees (Sec. 3, Fig. 3(c))
     keep = ("max_out", "max_in", "zero_in", "mean_out", "top5_out", "bottom5_in", "in_dist10")
     one = onng.adjust_degree(nbr, ln, 1, 0)
     info["graph_stats"] = {name: {key: round(v, 4) if isinstance(v, float) else v
@@ -768,7 +768,7 @@ def build_modes(onng, torch, a, Xd, Qd, knn_lists, seeds, gt):
 
 
 def tune_degrees(onng, torch, a, Xd, Qd, knn_lists, seeds, build, p_l=0.90, p_u=0.98):
-    """Sec. 4's optimisation of (e_o, e_i): every graph degree- and path-adjusted
+    """Sec. 2.6's optimisation of (e_o, e_i): every graph degree- and path-adjusted
     from the same exact kNN lists, scored by Eq. 2 (mean log10 distance
     computations over precision [p_l, p_u], every edge scanned) on the first
     --tune-queries queries, hill-climbed with a step of 5 from (e_o, e_i)."""
@@ -785,7 +785,7 @@ def tune_degrees(onng, torch, a, Xd, Qd, knn_lists, seeds, build, p_l=0.90, p_u=
                                                                 for e, (p, c) in samples]}
         return L
     climb = tune.hill_climb(loss, (a.e_o, a.e_i), step=5, lo=(0, 0), hi=(a.knn_k, a.knn_k))
-    line = {"what": "degree optimisation (Eq. 2 + hill climb, Sec. 4)", "workload": a.desc, "queries": nq,
+    line = {"what": "degree optimisation (Eq. 2 + hill climb, Sec. 2.6)", "workload": a.desc, "queries": nq,
             "k": a.k, "knng_k": a.knn_k, "precision_range": [p_l, p_u], "e_s": "all edges", "start": [a.e_o, a.e_i],
             "optimum": list(climb.best), "loss": round(climb.loss, 5),
             "path": [[eo, ei, round(l, 5)] for eo, ei, l in climb.path],

@@ -55,7 +55,7 @@ int onng_version(void);
 
 /* ------------------------------------------------------------------ kNN graph
  * Exact k nearest neighbours (the exact graph stands in for the approximate
- * kNN graph the paper derives from an ANNG, Sec. 2.5 / Algorithm ConstructGraph).
+ * kNN graph the paper derives from an ANNG, Sec. 2.6 / Algorithm ConstructGraph).
  *
  * onng_knn: for every query row r < nq, the k base points of X [n, d] nearest to
  * Q[r], as ids nbr [nq, k] int32 and Euclidean lengths len [nq, k] float32,
@@ -156,7 +156,7 @@ int onng_adjust_path_literal(const int64_t *row_ptr, const int32_t *col, const f
                              void *ws, size_t ws_bytes, onng_stream_t stream);
 
 /* ------------------------------------------------------------ graph statistics
- * The graph statistics of Table 4 (Sec. 3.2), a diagnostic of a built graph
+ * The graph statistics of Table 4 (Sec. 3.1), a diagnostic of a built graph
  * (not on the search path).  With m = ceil(n / 20) (5 % of the nodes, at least
  * one):
  *   mean_out    nnz / n
@@ -165,7 +165,7 @@ int onng_adjust_path_literal(const int64_t *row_ptr, const int32_t *col, const f
  *   in_dist10   mean length over the edges of the transposed graph with every
  *               node's incoming list cut to its 10 shortest (NaN without edges)
  *   max_out, max_in, zero_in   largest outdegree and indegree, and the count of
- *               nodes no edge reaches (the 1-NNG indegrees of Sec. 3.1, Fig. 1(b))
+ *               nodes no edge reaches (the 1-NNG indegrees of Sec. 3, Fig. 3(c))
  * row_ptr [n+1] must be a valid CSR (row_ptr[0] = 0, non-decreasing); col ids
  * outside [0, n) give ONNG_E_INVAL (after the kernels ran, ignoring them).
  * `out` is HOST memory; the call synchronises `stream`.  Degrees are counted as
@@ -207,7 +207,7 @@ int onng_index_load(const char *path, int64_t n, int32_t d, int64_t nnz, int64_t
 uint32_t onng_crc32(uint32_t crc, const void *data, size_t len);
 
 /* ---------------------------------------------------------------------- seeds
- * onng_seeds_random: the paper's random seeds (Sec. 3): n_seed distinct ids per
+ * onng_seeds_random: the paper's random seeds (Sec. 3.2, Fig. 5(a)): n_seed distinct ids per
  * query, query q drawing from the SplitMix64 stream that starts at state
  * global_seed + q * 2^32; a draw z maps to floor(z * n / 2^64), repeats are
  * redrawn.  When 2 * n_seed > n the seeds are 0 .. n_seed-1.  out [nq, n_seed].

@@ -14,7 +14,7 @@
  *
  * Functions and the passages they follow:
  *   oracle_knn            exact k-nearest neighbours (textbook definition; the
- *                         exact graph replaces the paper's ANNG-derived AKNNG, Sec. 2.5)
+ *                         exact graph replaces the paper's ANNG-derived AKNNG, Sec. 2.6)
  *   oracle_adjust_degree  static degree adjustment, Algorithm 2 (set form, Sec. 2.1)
  *   oracle_adjust_degree_sac  degree adjustment with constraints, Algorithm 3
  *   oracle_adjust_path    path adjustment, Algorithms 4/5 read order-free (Sec. 2.3)
@@ -27,7 +27,7 @@
  *                         how close the run came to a tie)
  *   oracle_search_probe   Algorithm 1 stopped after h expansions, with the features
  *                         the learned (eps, e_s) predictor reads (no paper counterpart)
- *   oracle_seeds_random   random seed rule (the paper's "rand" seeds, Sec. 3)
+ *   oracle_seeds_random   random seed rule (the paper's "rand" seeds, Sec. 3.2)
  *   oracle_seeds_pivot    nearest-pivot seed rule (stands in for the vp-tree
  *                         seeds of Sec. 2 / Table 5, which the paper leaves unspecified)
  *   oracle_bf16_round     bfloat16 round-to-nearest-even of float32 inputs
@@ -35,8 +35,8 @@
  *                         e4m3 encode / decode it rests on)
  *   oracle_mlp_*          the per-query (eps, e_s) predictor network (no paper
  *                         counterpart; the paper's fixed policy is Eq. 1)
- *   oracle_graph_stats    the graph statistics of Table 4 (Sec. 3.2) and the
- *                         indegree extremes of Sec. 3.1
+ *   oracle_graph_stats    the graph statistics of Table 4 (Sec. 3.1) and the
+ *                         indegree extremes of Sec. 3 (Fig. 3(c))
  */
 #include <math.h>
 #include <stdint.h>
@@ -1276,7 +1276,7 @@ void oracle_adam_step(double *P, const double *G, double *m, double *v, int64_t 
 }
 
 /* ------------------------------------------------------ graph statistics
- * Table 4 (Sec. 3.2).  With m = ceil(n / 20) (5 % of the nodes, at least one):
+ * Table 4 (Sec. 3.1).  With m = ceil(n / 20) (5 % of the nodes, at least one):
  *   out[0] mean outdegree            nnz / n
  *   out[1] mean top-5 % outdegree    mean outdegree of the m nodes of largest outdegree
  *   out[2] mean bottom-5 % indegree  mean indegree of the m nodes of smallest indegree

@@ -1,5 +1,5 @@
 // Exact k-nearest-neighbour lists (the exact kNN graph that replaces the
-// paper's approximate graph, Sec. 2.5) without materialising the n x n matrix.
+// paper's approximate graph, Sec. 2.6) without materialising the n x n matrix.
 //
 // knn_tile_kernel: a CTA owns 128 query rows and sweeps all base columns in
 // tiles of 128.  The tile of squared distances |q|^2 + |x|^2 - 2 q.x is formed

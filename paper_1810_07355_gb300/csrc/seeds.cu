@@ -1,6 +1,6 @@
 // Seed selection for the search.  The paper takes seeds from NGT's vp-tree
 // (Sec. 2, Table 5), which it does not specify, and also reports a random
-// variant (Sec. 3).  Two deterministic rules are provided:
+// variant (Sec. 3.2, Fig. 5(a)).  Two deterministic rules are provided:
 //   random: n_seed distinct ids per query from a SplitMix64 stream (Steele,
 //           Lea and Flood 2014) that starts at global_seed + q * 2^32; a draw z
 //           maps to floor(z * n / 2^64) and repeats are redrawn.

@@ -1,8 +1,8 @@
-// Graph statistics of Table 4 (Sec. 3.2): mean outdegree of the top 5 % of the
+// Graph statistics of Table 4 (Sec. 3.1): mean outdegree of the top 5 % of the
 // nodes by outdegree, mean indegree of the bottom 5 % by indegree, and the mean
 // indegree distance (edges of the transposed graph, each node's list cut to its
 // 10 shortest); plus the maximum indegree and the count of unreachable nodes
-// (indegree 0) that Sec. 3.1 and Fig. 1(b) discuss.
+// (indegree 0) that Sec. 3 and Fig. 3(c) discuss.
 //
 // Degrees are 32-bit.  The m-th largest (or smallest) degree is found by an
 // 8-bit radix select: four histogram passes over the nodes, each followed by a

@@ -7,11 +7,11 @@ computations over a target precision range [p_l, p_u] (Eq. 2),
 
 where C(e_o, e_i, p) is the mean number of distance computations per query at
 precision p (precision = recall@k here: the search returns k results).  The
-integral is estimated from searches (Sec. 4): a binary search on eps finds eps_l
+integral is estimated from searches (Sec. 2.6): a binary search on eps finds eps_l
 with precision in (p_l - 0.005, p_l] and eps_u with precision in [p_u, p_u + 0.005);
 [eps_l, eps_u] is cut into 9 equal parts, the 10 eps values are searched, and the
 trapezoidal rule integrates log10 C over the measured precisions.  Since L is
-convex in (e_o, e_i) (the paper's Fig. 5b), a hill climb with a step of 5 edges
+convex in (e_o, e_i) (the paper's Fig. 3(b)), a hill climb with a step of 5 edges (Sec. 3)
 finds the minimum.
 
 Readings (the paper is silent or garbled): the upper bracket is read as

@@ -67,7 +67,7 @@ def test_graph_stats_adjusted_graphs(onng):
         got = onng.graph_stats(*g)
         want = oracle.graph_stats(*(t.cpu().numpy() for t in g))
         assert_stats_equal(got, want)
-    # the 1-NNG's indegrees (Sec. 3.1): every node has one out-edge
+    # the 1-NNG's indegrees (Sec. 3, Fig. 3(c)): every node has one out-edge
     one = onng.adjust_degree(nbr, ln, 1, 0)
     got = onng.graph_stats(*one)
     assert got["mean_out"] == 1.0 and got["top5_out"] == 1.0

@@ -1,4 +1,4 @@
-"""Pins of the oracle's graph statistics (Table 4, Sec. 3.2): a star graph whose
+"""Pins of the oracle's graph statistics (Table 4, Sec. 3.1): a star graph whose
 values follow by hand, a ceil(5 %) case, and an independent numpy / scipy.sparse
 computation on random graphs."""
 import numpy as np
