@@ -890,7 +890,8 @@ def rows_near(ids, lens, o_ids, o_lens, rel=1e-5):
     distances are within `rel` (the distances agree position by position)."""
     same = (ids == o_ids).all(1)
     fin = np.isfinite(o_lens)
-    close = np.where(fin, np.abs(lens - o_lens) <= rel * np.abs(o_lens), np.isinf(lens))
+    with np.errstate(invalid="ignore"):  # inf - inf at padding: that branch is not taken
+        close = np.where(fin, np.abs(lens - o_lens) <= rel * np.abs(o_lens), np.isinf(lens))
     return same | close.all(1)
 
 

@@ -1,5 +1,5 @@
 """Host-side pieces of the benchmark: clock-sample parsing, the algorithmic-byte
-count behind the roofline, and recall@k."""
+count behind the roofline, recall@k, the precision-error and near-tie helpers."""
 import types
 
 import pytest
@@ -76,3 +76,41 @@ def test_parse_defaults_name_the_metric_workload():
     assert bench.parse(["--workload", "glove1m2"]).n == 1_200_000
     c = bench.common_config(a, 0.1, 1)
     assert c["workload"].startswith("sift-like n=1000000 d=128") and c["eps_fp32"] == 0.1
+
+
+def test_precision_error_by_hand():
+    """bfloat16 keeps 8 significant bits: 257 rounds (ties to even) to 256, so a
+    query at the origin sees 256 for a true 257, relative error 1/257; an FP8 e4m3
+    code of 17 (scale 1) decodes to 16 (steps of 2 at that exponent), error 1/17.
+    Byte-valued coordinates up to 256 are exact in bfloat16.  Padding ids (-1) are
+    not counted."""
+    X = torch.tensor([[257.0, 0.0], [17.0, 0.0], [200.0, 3.0]])
+    Q = torch.zeros((1, 2))
+    ids = torch.tensor([[0, 2, -1]])
+    e = bench.precision_error(torch, X, Q, ids)
+    assert e["pairs"] == 2 and e["max_rel"] == pytest.approx(1 / 257, rel=1e-12)
+    assert e["mean_rel"] == pytest.approx(0.5 / 257, rel=1e-12)
+    assert bench.precision_error(torch, X[2:], Q, torch.tensor([[0]]))["max_rel"] == 0.0
+    scale = torch.ones(2)
+    codes = X.to(torch.float8_e4m3fn).view(torch.uint8)
+    e8 = bench.precision_error(torch, X, Q, torch.tensor([[1]]), scale, codes)
+    assert e8["max_rel"] == pytest.approx(1 / 17, rel=1e-12)
+
+
+def test_rows_near_accepts_only_near_ties():
+    """A row passes when its ids equal the oracle's, or when every position's
+    distance agrees within 1e-5 relative (so swapped ids sit at near-equal
+    distances); an extra infinite pad must be infinite on both sides."""
+    import numpy as np
+    o_ids = np.array([[1, 2, 3], [1, 2, 3], [1, 2, -1]])
+    o_len = np.array([[1.0, 2.0, 3.0], [1.0, 2.0, 3.0], [1.0, 2.0, np.inf]])
+    ids = np.array([[1, 2, 3], [1, 3, 2], [1, 2, -1]])
+    near = np.array([[1.0, 2.0, 3.0], [1.0, 2.0 + 1e-6, 3.0], [1.0, 2.0, np.inf]])
+    assert bench.rows_near(ids, near, o_ids, o_len).tolist() == [True, True, True]
+    far = near.copy()
+    far[1, 1] = 2.1
+    assert bench.rows_near(ids, far, o_ids, o_len).tolist() == [True, False, True]
+    pad = near.copy()
+    pad[2, 2] = 5.0
+    assert bench.rows_near(np.array([[1, 2, 3], [1, 3, 2], [1, 2, 4]]), pad, o_ids, o_len).tolist() == \
+        [True, True, False]
