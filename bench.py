@@ -62,7 +62,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "queries/s at recall@10=0.95, 1M×128: learned+BF16 vs plain FP32 search"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "search_kernel_sift1m_traffic.json")
 NAMES = {"fp32": "plain fp32", "bf16": "fixed-eps bf16 + fp32 rerank", "fp8": "fixed-eps fp8 e4m3 + fp32 rerank",
          "eq1": "Eq. 1 policy (e_s = 10^(20 eps) + 30), bf16 + fp32 rerank",
          "bf16cap": "fixed-eps bf16 + fp32 rerank, expansions capped at the p99 of the uncapped run",
