@@ -207,10 +207,11 @@ int onng_index_load(const char *path, int64_t n, int32_t d, int64_t nnz, int64_t
 uint32_t onng_crc32(uint32_t crc, const void *data, size_t len);
 
 /* ---------------------------------------------------------------------- seeds
- * onng_seeds_random: the paper's random seeds (Sec. 3.2, Fig. 5(a)): n_seed distinct ids per
- * query, query q drawing from the SplitMix64 stream that starts at state
- * global_seed + q * 2^32; a draw z maps to floor(z * n / 2^64), repeats are
- * redrawn.  When 2 * n_seed > n the seeds are 0 .. n_seed-1.  out [nq, n_seed].
+ * onng_seeds_random: the paper's random seeds (Sec. 3.2, Fig. 5(a)): n_seed
+ * distinct ids per query, query q drawing from the SplitMix64 stream that
+ * starts at state global_seed + q * 2^32; a draw z maps to floor(z * n / 2^64),
+ * repeats are redrawn.  With m = min(n_seed, n): when 2 * m > n the seeds are
+ * 0 .. m-1; entries past m are -1.  out [nq, n_seed].
  *
  * onng_seeds_pivot: the n_seed nearest (distance, id) of the P = min(n_pivot, n)
  * pivots floor(t * n / P); stands in for the paper's vp-tree seeds (Sec. 2,
@@ -273,7 +274,7 @@ typedef struct {
     int32_t e_s;
     float eps;
     int32_t precision;
-    int32_t k_rerank;        /* bf16 only: candidates rescored in float32 (>= k) */
+    int32_t k_rerank;        /* bf16 and FP8: candidates rescored in float32 (>= k) */
     int32_t max_expansions;  /* 0: no cap; else per-query cap -> ONNG_FLAG_LIMIT */
     int32_t pool_cap;        /* candidate spill-pool entries per warp (0: 16384).  A query
                                 whose candidates outgrow the pool drops the ones that
