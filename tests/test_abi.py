@@ -250,3 +250,24 @@ def test_last_error_is_per_thread(lib):
     assert seen["knn"][0] == onng.ONNG_E_UNSUPPORTED and b"multiple of 4" in seen["knn"][1]
     assert seen["seeds"][0] == onng.ONNG_E_UNSUPPORTED and b"n_seed" in seen["seeds"][1]
     assert b"n_seed" not in seen["knn"][1] and b"multiple of 4" not in seen["seeds"][1]
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """With the library missing the binding raises on first use; nothing falls
+    back to another implementation (checked in a child process, so this one keeps
+    its loaded library)."""
+    import subprocess
+    import sys
+    child = (
+        "from paper_1810_07355_gb300 import onng\n"
+        "for call in (onng.load, lambda: onng.crc32(b'123456789')):\n"
+        "    try:\n"
+        "        call()\n"
+        "    except RuntimeError as e:\n"
+        "        assert 'not found' in str(e), e\n"
+        "    else:\n"
+        "        raise SystemExit('no error')\n"
+        "print('raised')\n")
+    env = dict(os.environ, ONNG_LIBRARY=str(tmp_path / "missing" / "libonng.so"), PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, "-c", child], cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and "raised" in r.stdout, r.stdout + r.stderr
