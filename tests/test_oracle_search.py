@@ -378,3 +378,43 @@ def test_expansion_cap(oracle_lib, one_cluster):
     for cap in (2, 5):
         _, _, c_st = oracle_lib.search(ptr, col, X, Q, 10, 6, 0.1, seeds, max_exp=cap)
         assert (c_st[:, 1] <= cap).all()
+
+
+def _capped_best_first(X64, q, ptr, col, seeds, k, e_s, cap):
+    """Brute force of Algorithm 1 at eps = inf stopped after `cap` expansions:
+    every scanned neighbour enters the candidates, so the run pops nodes in
+    (distance, id) order from everything seen and the results are the k nearest
+    of everything seen.  Returns (ids, distance computations, expansions,
+    candidate left)."""
+    seen = {}
+    for s in seeds:
+        seen.setdefault(int(s), float(np.sqrt(((X64[s] - q) ** 2).sum())))
+    cand = dict(seen)
+    expansions = 0
+    while cand and expansions < cap:
+        node = min(cand, key=lambda i: (cand[i], i))
+        del cand[node]
+        expansions += 1
+        for nb in col[ptr[node]:min(ptr[node] + e_s, ptr[node + 1])]:
+            nb = int(nb)
+            if nb not in seen:
+                seen[nb] = float(np.sqrt(((X64[nb] - q) ** 2).sum()))
+                cand[nb] = seen[nb]
+    ids = sorted(seen, key=lambda i: (seen[i], i))[:k]
+    return ids + [-1] * (k - len(ids)), len(seen), expansions, bool(cand)
+
+
+def test_expansion_cap_against_brute_force(oracle_lib, one_cluster):
+    """Caps of 2, 3 and 7 expansions at eps = inf: ids, distance computations,
+    expansions and the limit flag equal a brute-force best-first run stopped at
+    the cap."""
+    X, Q, (ptr, col, _) = one_cluster
+    seeds = oracle_lib.seeds_random(13, len(Q), len(X), 3)
+    X64 = X.astype(np.float64)
+    for cap in (2, 3, 7):
+        ids, _, st = oracle_lib.search(ptr, col, X, Q, 10, 6, np.inf, seeds, max_exp=cap)
+        for qi in range(len(Q)):
+            want, dc, ex, left = _capped_best_first(X64, Q[qi].astype(np.float64), ptr, col, seeds[qi], 10, 6,
+                                                    cap)
+            assert ids[qi].tolist() == want, (cap, qi)
+            assert (st[qi, 0], st[qi, 1], st[qi, 3]) == (dc, ex, 4 if left else 0), (cap, qi)
